@@ -1,0 +1,62 @@
+"""Critical hopping parameter kappa_c (oracle).
+
+Sec. 3 fixes kappa_c on each configuration as the kappa at which the real
+part of the smallest eigenvalue of A vanishes.  Every eigenvalue of
+A = 1 - kappa*D is 1 - kappa*lambda with lambda an eigenvalue of D, so for
+kappa > 0 the smallest real part is 1 - kappa*max Re lambda(D) and
+
+  kappa_c = 1 / max Re lambda(D).
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse.linalg as sla
+
+from . import dirac
+
+
+def kappa_c_dense(links, dims) -> float:
+    """kappa_c from the full spectrum of D (small lattices)."""
+    lam = np.linalg.eigvals(dirac.dense_D(links, dims))
+    return float(1.0 / np.max(lam.real))
+
+
+def kappa_c_bisect(links, dims, lo: float, hi: float, iters: int = 60) -> float:
+    """The workload's own definition: bisect kappa until min Re lambda(A) = 0.
+
+    Uses the dense matrix of A at every trial kappa, so it is for tiny
+    lattices only; it serves as an independent check of kappa_c_dense.
+    """
+    def min_re(kappa):
+        return np.min(np.linalg.eigvals(dirac.dense_A(links, dims, kappa)).real)
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        if min_re(mid) > 0:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def kappa_c_arnoldi(links, dims, tol: float = 1e-12, ncv: int = 40) -> float:
+    """kappa_c from the rightmost eigenvalue of D by implicitly restarted Arnoldi."""
+    n = 12 * links.shape[0]
+    v = links.shape[0]
+
+    def mv(x):
+        return dirac.hopping(links, x.reshape(v, 4, 3), dims).ravel()
+
+    op = sla.LinearOperator((n, n), matvec=mv, dtype=np.complex128)
+    rng = np.random.Generator(np.random.PCG64(7))
+    v0 = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    lam = sla.eigs(op, k=4, which="LR", tol=tol, ncv=ncv, v0=v0,
+                   return_eigenvectors=False)
+    return float(1.0 / np.max(lam.real))
+
+
+def kappa_c(links, dims) -> float:
+    if 12 * links.shape[0] <= 3072:
+        return kappa_c_dense(links, dims)
+    return kappa_c_arnoldi(links, dims)

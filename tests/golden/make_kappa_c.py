@@ -1,0 +1,41 @@
+"""Write kappa_c.json: the critical kappa of every preset gauge field.
+
+kappa_c is computed by the CPU oracle only (rightmost eigenvalue of the
+hopping matrix D, kappa_c = 1 / max Re lambda(D)); the CUDA path never
+contributes to it.  Run from the repository root:
+
+    python tests/golden/make_kappa_c.py [preset ...]
+"""
+import json
+import os
+import sys
+import time
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)))))
+
+from inputs import lattice as L          # noqa: E402
+from oracle import kappa                 # noqa: E402
+
+OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "kappa_c.json")
+
+
+def main(names):
+    table = {}
+    if os.path.exists(OUT):
+        with open(OUT) as f:
+            table = json.load(f)
+    for name in names:
+        cfg = L.CONFIGS[name]
+        t0 = time.time()
+        U = L.gauge_field(cfg.dims, cfg.eps, L.link_seed(cfg))
+        kc = kappa.kappa_c(U, cfg.dims)
+        table[name] = {"dims": list(cfg.dims), "eps": cfg.eps,
+                       "link_seed": L.link_seed(cfg), "kappa_c": kc,
+                       "method": "dense eig" if 12 * U.shape[0] <= 3072 else "Arnoldi (eigs LR)"}
+        print(f"{name}: kappa_c = {kc!r}  ({time.time() - t0:.0f} s)", flush=True)
+        with open(OUT, "w") as f:
+            json.dump(table, f, indent=1, sort_keys=True)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:] or list(L.CONFIGS))
