@@ -1,0 +1,481 @@
+#!/usr/bin/env python
+"""Benchmark: D-BiCGStab solves/s at relative residual 1e-10 on one GB300.
+
+Workload (default): 16^4 periodic lattice, complex128, links exp(i*0.5*H),
+kappa = 0.99 kappa_c.  One step is the whole method on one batch:
+GMRES-DR(80,40) on a Z4 source to 1e-10 (giving V), the deflation space
+(W = A V, LU of U^dagger A V with U = gamma5 V), and D-BiCGStab(40) on 10
+further Z4 sources, all to a true relative residual of 1e-10.  value =
+D-BiCGStab solves per second with the whole step in the denominator.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+For N > 1 launch under torchrun: every rank solves its own, independently
+seeded batch on its own GPU (no collective on the data path: replicas,
+weak scaling); the step time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from inputs import lattice as L  # noqa: E402
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+KAPPA_TABLE = os.path.join(ROOT, "tests", "golden", "kappa_c.json")
+ORACLE_COUNTS = os.path.join(ROOT, "tests", "golden", "oracle_counts_16x16x16x16.json")
+# FP64 ALU peak derived from unit counts and clock: 2 DFMA (4 flops) per clock
+# per SM on 152 SMs at the 2070 MHz maximum SM clock = 1.2586 TFLOP/s, the
+# 1.25 TFLOP/s nominal figure; a DFMA throughput probe measured 1.188 TFLOP/s
+# at 1995 MHz, i.e. the same 4 flops/clk/SM.
+FP64_FLOPS_PER_CLK_PER_SM = 4
+SMS = 152
+SM_MAX_MHZ = 2070.0
+
+DSLASH_FLOPS_PER_SITE = 1368      # 1320 hopping + 48 for 1 - kappa*D
+DSLASH_BYTES_PER_SITE = 960       # 192 in + 192 out + 4 links x 144 (FP64)
+METRIC = "D-BiCGStab solves/s at rel. residual 1e-10; dslash GB/s vs HBM roofline"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--config", default="wilson_16x16x16x16")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def load_json(path, default=None):
+    if not os.path.exists(path):
+        return default
+    with open(path) as f:
+        return json.load(f)
+
+
+def kappa_for(cfg):
+    table = load_json(KAPPA_TABLE, {})
+    if cfg.name not in table:
+        raise SystemExit(f"kappa_c of {cfg.name} missing: run tests/golden/make_kappa_c.py")
+    return cfg.kappa_factor * table[cfg.name]["kappa_c"]
+
+
+def rank_sources(cfg, rank, count):
+    """Right-hand sides of this rank: independent seeds per rank."""
+    out = []
+    for j in range(count):
+        seed = L.rhs_seed(cfg, j) + 100000 * rank
+        if cfg.rhs_kind == "z4":
+            out.append(L.z4_spinor(cfg.dims, seed))
+        else:
+            out.append(L.gaussian_spinor(cfg.dims, seed))
+    return np.stack(out)
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax = float(p[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, p[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+
+def _oracle_sample(cfg_name, kappa, budget_s):
+    """Time the oracle's building blocks on the full workload (one thread)."""
+    from oracle import dirac
+    cfg = L.CONFIGS[cfg_name]
+    U = L.gauge_field(cfg.dims, cfg.eps, L.link_seed(cfg))
+    v = L.volume(cfg.dims)
+    A = lambda x: dirac.apply_A(U, x.reshape(v, 4, 3), cfg.dims, kappa).ravel()
+    b = L.source(cfg, 1).ravel()
+    t0 = time.perf_counter()
+    # BiCGStab iteration: 2 applies + the vector updates and dots of the oracle
+    from oracle import krylov
+    ti = []
+    while not ti or (time.perf_counter() - t0 < budget_s / 2 and len(ti) < 5):
+        t = time.perf_counter()
+        krylov.bicgstab(A, b, tol=1e-300, max_iter=2, max_restarts=0)
+        ti.append((time.perf_counter() - t) / 2)
+    t_iter = min(ti)
+    # Arnoldi step with CGS2 against j vectors, j = k and j = m - 1
+    n = b.size
+    Vb = np.zeros((cfg.m + 1, n), dtype=np.complex128)
+    rng = np.random.Generator(np.random.PCG64(3))
+    Vb[:] = rng.standard_normal((cfg.m + 1, n))
+    ta = {}
+    for j in (cfg.k, cfg.m - 1):
+        t = time.perf_counter()
+        w = A(Vb[j])
+        h = Vb[: j + 1].conj() @ w
+        w = w - Vb[: j + 1].T @ h
+        h2 = Vb[: j + 1].conj() @ w
+        w = w - Vb[: j + 1].T @ h2
+        _ = np.sqrt(np.vdot(w, w).real)
+        ta[j] = time.perf_counter() - t
+    t_apply = []
+    for _ in range(2):
+        t = time.perf_counter()
+        A(b)
+        t_apply.append(time.perf_counter() - t)
+    return {"t_iter": t_iter, "t_arnoldi": ta, "t_apply": min(t_apply),
+            "elapsed": time.perf_counter() - t0}
+
+
+def _oracle_sample_entry(q, cfg_name, kappa, budget_s):
+    q.put(_oracle_sample(cfg_name, kappa, budget_s))
+
+
+THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+def oracle_timing(cfg, kappa, budget_s=20.0):
+    """Run the sample in a spawned process limited to one BLAS thread (the
+    variables are set before the spawn so the child's numpy sees them)."""
+    saved = {v: os.environ.get(v) for v in THREAD_VARS}
+    for v in THREAD_VARS:
+        os.environ[v] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        q = ctx.Queue()
+        p = ctx.Process(target=_oracle_sample_entry, args=(q, cfg.name, kappa, budget_s))
+        p.start()
+        res = q.get()
+        p.join()
+    finally:
+        for v, val in saved.items():
+            if val is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = val
+    return res
+
+
+def extrapolate_step(cfg, t, counts):
+    """CPU seconds for one step of the workload from the per-block timings."""
+    m, k = cfg.m, cfg.k
+    cycles = counts["gmresdr_cycles"]
+    t_lo, t_hi = t["t_arnoldi"][k], t["t_arnoldi"][m - 1]
+    slope = (t_hi - t_lo) / max(1, (m - 1 - k))
+
+    def arn(j):
+        return t_lo + slope * (j - k)
+    first = sum(max(arn(j), t["t_apply"]) for j in range(m))
+    later = sum(arn(j) for j in range(k, m))
+    gmres = first + later * max(0, cycles - 1)
+    defl = k * t["t_apply"]
+    bicg = sum(counts["dbicgstab_iters"]) * t["t_iter"]
+    return gmres + defl + bicg
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def gpu_arm(args, cfg, rank, world, local_rank):
+    import torch
+    import paper_0710_1988_gb300 as wdl
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    kappa = kappa_for(cfg)
+    U = L.gauge_field(cfg.dims, cfg.eps, L.link_seed(cfg))
+    v = L.volume(cfg.dims)
+    n = 12 * v
+    src = rank_sources(cfg, rank, cfg.n_rhs + 1)
+    b0 = torch.from_numpy(src[0].ravel()).to(dev)
+    B = torch.from_numpy(src[1:].reshape(cfg.n_rhs, n)).to(dev)
+    x0 = torch.zeros_like(b0)
+    X = torch.zeros_like(B)
+    V = torch.zeros(cfg.k * n, dtype=torch.complex128, device=dev)
+    op = wdl.WilsonOperator(cfg.dims, torch.from_numpy(U).to(dev), kappa)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream(dev)
+
+    def step(b0_, x0_, B_, X_):
+        x0_.zero_() if hasattr(x0_, "zero_") else x0_.fill(0)
+        X_.zero_() if hasattr(X_, "zero_") else X_.fill(0)
+        rc, st, _, theta = op.gmresdr(b0_, x0_, cfg.m, cfg.k, cfg.tol, 400000, V_out=V)
+        defl = op.deflation(V, cfg.k)
+        rc2, sts = op.dbicgstab(B_, X_, defl, tol=cfg.tol)
+        defl.close()
+        if rc != 0 or rc2 != 0 or not all(s["converged"] for s in sts):
+            raise RuntimeError(f"solve did not converge: gmresdr rc={rc}, dbicgstab rc={rc2}")
+        return st, sts
+
+    for _ in range(args.warmup):
+        step(b0, x0, B, X)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs, dslash launches timed live
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    op.profile(mask=0x1)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ms_steps, last = [], None
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        last = step(b0, x0, B, X)
+        e1.record(stream)
+        e1.synchronize()
+        ms_steps.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    prof_live = op.profile_read()
+    op.profile(mask=0)
+    clk = clocks.stop()
+    total_ms = sum(ms_steps)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # ---- one more step with every kernel category timed: the breakdown
+    op.profile(mask=0xF)
+    step(b0, x0, B, X)
+    prof_all = op.profile_read()
+    op.profile(mask=0)
+
+    gst, sts = last
+    counts = {"gmresdr_mvp": gst["mvp"], "gmresdr_cycles": gst["cycles"],
+              "dbicgstab_mvp": [s["mvp"] for s in sts],
+              "dbicgstab_iters": [s["iters"] for s in sts],
+              "true_rel_res_max": max(s["true_rel_res"] for s in sts),
+              "gmresdr_true_rel_res": gst["true_rel_res"]}
+
+    # ---- e2e: the same step through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+        b0h = pin(src[0].ravel().copy())
+        Bh = pin(src[1:].reshape(cfg.n_rhs, n).copy())
+        x0h = pin(np.zeros(n, dtype=np.complex128))
+        Xh = pin(np.zeros((cfg.n_rhs, n), dtype=np.complex128))
+        step(b0h, x0h, Bh, Xh)  # warm the staging buffers
+        if world > 1:
+            torch.distributed.barrier()
+        wall = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            step(b0h, x0h, Bh, Xh)
+            torch.cuda.synchronize()
+            wall.append(time.perf_counter() - t)
+        tot = sum(wall)
+        if world > 1:
+            tt = torch.tensor([tot], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            tot = float(tt.item())
+        h2d = (2 + 2 * cfg.n_rhs) * n * 16      # b0, x0, B, X0 staged in
+        d2h = (1 + cfg.n_rhs) * n * 16          # x and X copied back
+        e2e = {"value": cfg.n_rhs * args.steps * world / tot, "unit": "solves/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": 1000 * tot / args.steps}
+    op.close()
+    return {"total_ms": total_ms, "ms_steps": ms_steps, "prof_live": prof_live,
+            "prof_all": prof_all, "counts": counts, "clocks": clk, "e2e": e2e,
+            "kappa": kappa, "n": n, "volume": v}
+
+
+def roofline(res, peaks, fp64_peak):
+    live = res["prof_live"]
+    launches = live["dslash"]["launches"]
+    ms = live["dslash"]["ms"]
+    sites = live["dslash_site_updates"]
+    avg_ms = ms / max(1, launches)
+    sites_per_launch = sites / max(1, launches)
+    flops = DSLASH_FLOPS_PER_SITE * sites_per_launch
+    tflops = flops / (avg_ms * 1e-3) / 1e12
+    gbs = DSLASH_BYTES_PER_SITE * sites_per_launch / (avg_ms * 1e-3) / 1e9
+    out = {
+        "kernel": "wilson_f64_kernel (FP64 dslash)",
+        "bound": "alu",
+        "achieved": round(tflops, 4),
+        "peak": fp64_peak["tflops"],
+        "unit": "TFLOP/s",
+        "frac": round(tflops / fp64_peak["tflops"], 4),
+        "peak_source": fp64_peak["source"],
+        "traffic": None,
+        "algorithmic_flops_per_launch": flops,
+        "avg_launch_ms": avg_ms,
+        "launches": launches,
+        "hbm_view": {"achieved_gbs": round(gbs, 1), "peak_gbs": peaks.get("hbm_gbs"),
+                     "frac": round(gbs / peaks["hbm_gbs"], 4) if peaks.get("hbm_gbs") else None,
+                     "algorithmic_bytes_per_launch": DSLASH_BYTES_PER_SITE * sites_per_launch},
+    }
+    return out
+
+
+def main():
+    args = parse()
+    cfg = L.CONFIGS[args.config]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return reference_arm(args, cfg, rank, world)
+
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group(backend="nccl")
+    res = gpu_arm(args, cfg, rank, world, local_rank)
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    peaks = load_json(MEASURED_PEAKS, {}) or {}
+    fp64_peak = {"tflops": round(FP64_FLOPS_PER_CLK_PER_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12, 4),
+                 "source": "derived: 4 FP64 flops/clk/SM x 152 SMs x 2070 MHz (= nominal 1.25 TFLOP/s)"}
+    steps = args.steps
+    value = cfg.n_rhs * steps * world / (res["total_ms"] * 1e-3)
+    line = {
+        "metric": METRIC,
+        "value": round(value, 4),
+        "unit": "solves/s",
+        "n_gpus": world,
+        "steps": steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(res["total_ms"] / steps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic: SU(3) links exp(i*0.5*H) (seed 1001), Z4 sources; no dataset",
+        "config": {
+            "workload": f"{cfg.name}: GMRES-DR({cfg.m},{cfg.k}) on 1 Z4 source + D-BiCGStab({cfg.k}) "
+                        f"on {cfg.n_rhs} Z4 sources, tol {cfg.tol:g}, kappa = {cfg.kappa_factor} kappa_c",
+            "lattice": list(cfg.dims), "kappa": res["kappa"], "m": cfg.m, "k": cfg.k,
+            "rhs_per_step": cfg.n_rhs, "parallelism": f"replicas x{world}",
+            "l2": "256 MB L2 flush before every step; step working set (1.0 GB Krylov basis, "
+                  "0.9 GB BiCGStab batch) exceeds the 129 MB L2",
+        },
+        "gpu_launches": None,
+        "roofline": roofline(res, peaks, fp64_peak),
+        "clocks": res["clocks"],
+        "e2e": res["e2e"],
+        "counts": res["counts"],
+        "kernel_breakdown_ms": {k: v for k, v in res["prof_all"].items() if k != "dslash_site_updates"},
+    }
+    pa = res["prof_all"]
+    line["gpu_launches"] = int(sum(pa[c]["launches"] for c in ("dslash", "stream", "tall_skinny", "dense")) * steps)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t = oracle_timing(cfg, res["kappa"])
+        counts = load_json(ORACLE_COUNTS) or res["counts"]
+        src = "oracle's own counts" if os.path.exists(ORACLE_COUNTS) else "GPU run's counts"
+        t_step = extrapolate_step(cfg, t, counts)
+        line["cpu_baseline"] = {
+            "value": round(cfg.n_rhs / t_step, 6), "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle (numpy FP64, 1 thread) timed on the full {cfg.name} workload: "
+                       f"BiCGStab iteration {t['t_iter']:.3f} s, Arnoldi+CGS2 step at j={cfg.k} "
+                       f"{t['t_arnoldi'][cfg.k]:.3f} s and j={cfg.m - 1} {t['t_arnoldi'][cfg.m - 1]:.3f} s, "
+                       f"apply {t['t_apply']:.3f} s; step time {t_step:.1f} s extrapolated with the "
+                       f"{src} ({counts['gmresdr_cycles']} GMRES-DR cycles, "
+                       f"{sum(counts['dbicgstab_iters'])} BiCGStab iterations); sample took "
+                       f"{t['elapsed']:.1f} s"),
+        }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def reference_arm(args, cfg, rank, world):
+    """The oracle on the host cores, same metric and workload, bounded samples."""
+    if rank != 0:
+        return
+    kappa = kappa_for(cfg)
+    counts = load_json(ORACLE_COUNTS)
+    if counts is None:
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "oracle iteration counts for this workload not recorded"}))
+        return
+    budget = 8.0
+    for _ in range(args.warmup):
+        oracle_timing(cfg, kappa, budget_s=budget)
+    times, samples = [], []
+    for _ in range(args.steps):
+        t = oracle_timing(cfg, kappa, budget_s=budget)
+        samples.append(t)
+        times.append(extrapolate_step(cfg, t, counts))
+    t_step = statistics.median(times)
+    value = cfg.n_rhs / t_step
+    line = {
+        "impl": "reference",
+        "metric": METRIC, "value": round(value, 6), "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000 * t_step, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (same inputs as the GPU arm)",
+        "config": {"workload": cfg.name, "lattice": list(cfg.dims), "m": cfg.m, "k": cfg.k,
+                   "rhs_per_step": cfg.n_rhs},
+        "cpu_baseline": {"value": round(value, 6), "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": "per step: oracle BiCGStab iterations, two Arnoldi+CGS2 steps and "
+                                   "applies on the full workload, extrapolated with the oracle's own "
+                                   "recorded cycle and iteration counts"},
+        "e2e": {"value": round(value, 6), "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

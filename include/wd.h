@@ -1,0 +1,182 @@
+/*
+ * wd.h - C ABI of the GB300 deflated-BiCGStab library (libwd.so).
+ *
+ * Method: Abdel-Rehim, Morgan, Wilcox, "Deflated BiCGStab for linear
+ * equations in QCD problems" (Lattice 2007).  The first right-hand side is
+ * solved by GMRES-DR(m,k), which also yields k approximate right
+ * eigenvectors V (Sec. 1).  Every later right-hand side gets the k x k
+ * left-right projection (U^dagger A V) y = U^dagger r0, x0 += V y, with
+ * U = gamma5 V from gamma5 A gamma5 = A^dagger, and then plain BiCGStab
+ * (Sec. 2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Lattice extents lat = {Lx, Ly, Lz, Lt}, all >= 1, periodic; volume
+ *    V = Lx*Ly*Lz*Lt, vector length n = 12*V complex numbers.
+ *  - Site index s = x + Lx*(y + Ly*(z + Lz*t)).
+ *  - Spinor layout (boundary): complex128 (two doubles, re then im)
+ *    psi[s][sigma][a], spin sigma = 0..3, colour a = 0..2, i.e. 192 bytes
+ *    per site; a batch of nrhs spinors is nrhs such arrays back to back.
+ *  - Gauge layout (boundary): complex128 U[s][mu][a][b], mu = 0..3 for
+ *    x, y, z, t, 576 bytes per site.
+ *  - Operator: A = 1 - kappa*D + i*mu*gamma5 with the Wilson hopping term
+ *      (D psi)(x) = sum_mu (1 - gamma_mu) U_mu(x) psi(x+mu)
+ *                         + (1 + gamma_mu) U_mu(x-mu)^dagger psi(x-mu),
+ *    chiral gamma basis, gamma5 = diag(1, 1, -1, -1).  mu = 0 is plain
+ *    Wilson (Sec. 1); mu != 0 is the twisted-mass operator of Sec. 4.
+ *  - Pointers named "device or host" are classified with
+ *    cudaPointerGetAttributes: device (or managed) memory is used in
+ *    place; host memory is staged through library-owned device buffers and
+ *    the call then synchronises `stream` before it returns.  All other
+ *    vector pointers must be device memory.  The caller owns every buffer
+ *    it passes; the library never keeps a caller pointer after a call.
+ *  - All GPU work is enqueued on `stream` (a cudaStream_t; NULL is the
+ *    legacy default stream).  Calls that report results to the host
+ *    (solvers, stats) synchronise that stream.  One handle must not be
+ *    used from two streams or threads at once.
+ *  - Every function returns a status; nothing aborts or throws across the
+ *    ABI.  On error, wd_last_error_detail() gives a one-line reason.
+ */
+#ifndef WD_H
+#define WD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wd_context *wd_handle;
+typedef struct wd_deflation_space *wd_deflation;
+typedef struct CUstream_st *wd_stream;   /* identical to cudaStream_t */
+
+enum wd_status {
+  WD_OK = 0,
+  WD_BAD_ARG = 1,              /* invalid size, pointer or parameter */
+  WD_NOT_CONVERGED = 2,        /* tolerance not reached; x and stats still
+                                  written (the paper's "F", Sec. 3) */
+  WD_BREAKDOWN = 3,            /* a Krylov scalar vanished (rho, <r_hat,v>) */
+  WD_SINGULAR_PROJECTION = 4,  /* U^dagger A V numerically singular */
+  WD_TIMEOUT = 5,              /* a bounded device-side wait expired */
+  WD_CUDA_ERROR = 6,           /* a CUDA call failed (see detail) */
+  WD_OUT_OF_MEMORY = 7
+};
+
+/* Per-solve statistics.  mvp counts the matrix-vector products inside the
+ * Krylov iteration, as the paper's tables do (Sec. 3, Sec. 4); mvp_extra
+ * counts products spent on initial and true residuals and on setup. */
+typedef struct {
+  long long mvp;
+  long long mvp_extra;
+  int iters;         /* BiCGStab iterations (2 MVPs each) */
+  int cycles;        /* GMRES-DR cycles */
+  int restarts;      /* BiCGStab restarts from the true residual */
+  int converged;     /* 1 if true residual <= tol */
+  int breakdown;
+  double rel_res;    /* recursive (BiCGStab) or least-squares (GMRES-DR)
+                        residual norm / ||b|| */
+  double true_rel_res;  /* ||b - A x|| / ||b|| recomputed at the end */
+  double ms;         /* wall time of the call on `stream` */
+} wd_stats;
+
+/* ---------------------------------------------------------- operator */
+
+/* Create a handle for A = 1 - kappa*D + i*mu*gamma5 on lattice `lat`.
+ * links: device or host pointer, boundary gauge layout, V*4*9 complex128;
+ * the handle copies it into its own device storage, so the caller may
+ * free it afterwards.  Sec. 1 (Wilson matrix), Sec. 4 (twisted mass). */
+int wd_create(const int lat[4], const void *links, double kappa, double mu,
+              wd_handle *out);
+
+/* Change kappa and mu of an existing handle (no data movement). */
+int wd_set_params(wd_handle h, double kappa, double mu);
+
+/* out = A in (dagger = 0) or A^dagger in (dagger = 1) for nrhs spinors.
+ * in, out: device pointers, boundary spinor layout, nrhs*n complex128
+ * each, in != out (no aliasing).  Sec. 1. */
+int wd_apply(wd_handle h, const void *in, void *out, int nrhs, int dagger,
+             wd_stream stream);
+
+/* ---------------------------------------------------------- solvers */
+
+/* GMRES-DR(m,k) for A x = b (Sec. 1, Sec. 3; Morgan's deflated restarting).
+ *  b:        device or host, n complex128.
+ *  x:        device or host, n complex128; initial guess in, solution out.
+ *  m, k:     subspace size and number of kept harmonic Ritz vectors,
+ *            1 <= m <= 80, 0 <= k < m, m <= n.
+ *  tol:      stop when the least-squares residual norm / ||b - A x0|| <= tol,
+ *            tested at the end of each cycle.
+ *  max_mv:   budget of counted MVPs (m for the first cycle, m-k later).
+ *  V_out:    NULL or device, k*n complex128: orthonormal basis of the k
+ *            harmonic Ritz vectors after the final restart (Sec. 2's V).
+ *  Hbar_out: NULL or host, (k+1)*k complex128 row-major: A V = V_{k+1} Hbar.
+ *  theta_out:NULL or host, k complex128: the kept harmonic Ritz values,
+ *            ordered by (|theta|, Re, Im).
+ *  stats:    NULL or host.
+ * Returns WD_OK, WD_NOT_CONVERGED (x, V still written) or an error. */
+int gmresdr_solve(wd_handle h, const void *b, void *x, int m, int k,
+                  double tol, int max_mv, void *V_out, void *Hbar_out,
+                  void *theta_out, wd_stats *stats, wd_stream stream);
+
+/* Build the deflation space of Sec. 2 once for many right-hand sides:
+ * W = A V (k MVPs), G = U^dagger A V and its LU factors.
+ *  V: device, k*n complex128, orthonormal columns (e.g. from gmresdr_solve).
+ *  U: NULL for U = gamma5 V (Sec. 1), else device, k*n complex128.
+ * The handle copies V and U; 1 <= k <= 128. */
+int wd_deflation_create(wd_handle h, const void *V, const void *U, int k,
+                        wd_deflation *out, wd_stream stream);
+void wd_deflation_destroy(wd_deflation d);
+
+/* D-BiCGStab(k) for A X = B, nrhs right-hand sides batched (Sec. 2):
+ * x0 = X on entry, r0 = B - A x0, y = (U^dagger A V)^{-1} U^dagger r0,
+ * x0 += V y, then BiCGStab from x0 for every right-hand side at once,
+ * each with its own scalars and convergence mask.  d = NULL gives plain
+ * BiCGStab.  Convergence: ||r|| / ||b|| <= tol on the recursive residual,
+ * then on the true residual (restart from it at most 3 times).
+ *  B: device or host, nrhs*n complex128.  X: device or host, in/out.
+ *  stats: NULL or host array of nrhs.
+ * Returns WD_OK when every system converged, else WD_NOT_CONVERGED or
+ * WD_BREAKDOWN (solutions and stats still written). */
+int dbicgstab_solve_deflated(wd_handle h, wd_deflation d, const void *B,
+                             void *X, int nrhs, double tol, int max_iter,
+                             wd_stats *stats, wd_stream stream);
+
+/* One-shot form: wd_deflation_create(V, U, k) + dbicgstab_solve_deflated +
+ * destroy.  k = 0 (V = U = NULL) is plain BiCGStab. */
+int dbicgstab_solve(wd_handle h, const void *B, void *X, int nrhs,
+                    const void *V, const void *U, int k, double tol,
+                    int max_iter, wd_stats *stats, wd_stream stream);
+
+/* ---------------------------------------------------------- instrumentation */
+
+/* Kernel timing, not part of the paper's method: CUDA events bracket every
+ * launch of the enabled categories on the launching stream.  Categories:
+ * 0 Wilson apply (dslash), 1 streaming vector kernels and scalar
+ * finalizers, 2 tall-skinny products (V^dagger W, W += V Y), 3 single-block
+ * dense kernels (LU, GMRES-DR cycle end). */
+typedef struct {
+  long long launches[4];
+  double ms[4];                    /* summed launch durations */
+  long long dslash_site_updates;   /* lattice sites x systems the dslash
+                                      launches actually processed */
+} wd_profile;
+
+/* Enable the categories whose bit is set in mask (0 disables) and reset the
+ * counters.  Timing adds two event records per launch of an enabled kind. */
+int wd_profile_enable(wd_handle h, unsigned mask);
+/* Resolve the recorded events (waits for them) and copy the counters. */
+int wd_profile_read(wd_handle h, wd_profile *out);
+
+/* ---------------------------------------------------------- housekeeping */
+
+void wd_destroy(wd_handle h);
+const char *wd_error_string(int status);
+/* Copies the last error's one-line reason (this thread) into buf. Returns
+ * its full length. */
+int wd_last_error_detail(char *buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WD_H */

@@ -1,0 +1,178 @@
+"""Deflated BiCGStab for Wilson-Dirac systems on GB300: Python binding.
+
+A thin ctypes layer over libwd.so (C ABI in include/wd.h).  It only
+marshals arguments: every step of every solve runs in the library's CUDA
+kernels.  Tensors are torch complex128 CUDA tensors (device pointers) or
+complex128 numpy arrays (host pointers, staged by the library), laid out
+as [nrhs][site][spin][colour] with site = x + Lx*(y + Ly*(z + Lz*t)).
+
+Method: Abdel-Rehim, Morgan, Wilcox, "Deflated BiCGStab for linear
+equations in QCD problems" (Lattice 2007): GMRES-DR(m,k) for the first
+right-hand side (Sec. 1), then the left-right projection with U = gamma5 V
+and BiCGStab for the others (Sec. 2).
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import _lib
+from ._lib import WdError, WdStats, check, lib  # noqa: F401
+
+__all__ = ["WilsonOperator", "Deflation", "WdError", "WdStats", "lib"]
+
+
+def _ptr(a) -> int:
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if str(a.dtype) != "torch.complex128":
+            raise TypeError(f"expected complex128, got {a.dtype}")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.complex128 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("expected a C-contiguous complex128 array")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _numel(a) -> int:
+    return a.numel() if hasattr(a, "numel") else a.size
+
+
+def _stream(stream, *arrays) -> Optional[int]:
+    if stream is not None:
+        return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+    for a in arrays:
+        if hasattr(a, "is_cuda") and a.is_cuda:
+            import torch
+            return int(torch.cuda.current_stream(a.device).cuda_stream)
+    return None
+
+
+class WilsonOperator:
+    """A = 1 - kappa*D + i*mu*gamma5 on a periodic lattice dims = (Lx, Ly, Lz, Lt)."""
+
+    def __init__(self, dims: Sequence[int], links, kappa: float, mu: float = 0.0):
+        self.dims = tuple(int(d) for d in dims)
+        self.volume = int(np.prod(self.dims))
+        self.n = 12 * self.volume
+        if _numel(links) != 36 * self.volume:
+            raise ValueError("links must hold V*4*3*3 complex numbers")
+        self.kappa = float(kappa)
+        self.mu = float(mu)
+        lat = (ctypes.c_int * 4)(*self.dims)
+        h = ctypes.c_void_p()
+        check(lib().wd_create(lat, _ptr(links), self.kappa, self.mu, ctypes.byref(h)))
+        self._h = h
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().wd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def profile(self, mask: int = 0xF):
+        """Start timing the kernel categories in mask (bit 0 dslash, 1 streaming,
+        2 tall-skinny, 3 dense); mask = 0 stops.  Counters restart from zero."""
+        check(lib().wd_profile_enable(self._h, int(mask)))
+
+    def profile_read(self) -> dict:
+        p = _lib.WdProfile()
+        check(lib().wd_profile_read(self._h, ctypes.byref(p)))
+        return p.as_dict()
+
+    def set_params(self, kappa: float, mu: float = 0.0):
+        self.kappa, self.mu = float(kappa), float(mu)
+        check(lib().wd_set_params(self._h, self.kappa, self.mu))
+
+    def _nrhs(self, a) -> int:
+        n = _numel(a)
+        if n % self.n:
+            raise ValueError("vector length is not a multiple of 12*V")
+        return n // self.n
+
+    # -- operator
+    def apply(self, x, out, dagger: bool = False, stream=None):
+        """out = A x (or A^dagger x); x, out CUDA complex128, nrhs*12V elements."""
+        nrhs = self._nrhs(x)
+        if _numel(out) != _numel(x):
+            raise ValueError("out must match x")
+        check(lib().wd_apply(self._h, _ptr(x), _ptr(out), nrhs, 1 if dagger else 0,
+                             _stream(stream, x, out)))
+        return out
+
+    # -- solvers
+    def gmresdr(self, b, x, m: int, k: int, tol: float = 1e-10, max_mv: int = 100000,
+                V_out=None, stream=None):
+        """GMRES-DR(m,k): x (initial guess in, solution out).  Returns
+        (status, stats, Hbar (k+1,k) numpy, theta (k,) numpy); V_out, if given,
+        a CUDA tensor of k*12V elements, receives the deflation basis."""
+        st = WdStats()
+        hbar = np.zeros((k + 1, max(k, 1)), dtype=np.complex128)
+        theta = np.zeros(max(k, 1), dtype=np.complex128)
+        rc = lib().gmresdr_solve(
+            self._h, _ptr(b), _ptr(x), int(m), int(k), float(tol), int(max_mv),
+            _ptr(V_out) if V_out is not None else None,
+            hbar.ctypes.data if k > 0 else None, theta.ctypes.data if k > 0 else None,
+            ctypes.byref(st), _stream(stream, b, x))
+        check(rc, allow=(_lib.WD_OK, _lib.WD_NOT_CONVERGED))
+        return rc, st.as_dict(), hbar[:, :k], theta[:k]
+
+    def deflation(self, V, k: int, U=None, stream=None) -> "Deflation":
+        return Deflation(self, V, k, U, stream)
+
+    def dbicgstab(self, B, X, deflation: Optional["Deflation"] = None, tol: float = 1e-10,
+                  max_iter: int = 100000, stream=None):
+        """D-BiCGStab(k) for every right-hand side in B at once (deflation=None:
+        plain BiCGStab).  X holds the initial guesses and receives the solutions.
+        Returns (status, [stats per right-hand side])."""
+        nrhs = self._nrhs(B)
+        sts = (WdStats * nrhs)()
+        rc = lib().dbicgstab_solve_deflated(
+            self._h, deflation._d if deflation is not None else None, _ptr(B), _ptr(X),
+            nrhs, float(tol), int(max_iter), sts, _stream(stream, B, X))
+        check(rc, allow=(_lib.WD_OK, _lib.WD_NOT_CONVERGED, _lib.WD_BREAKDOWN))
+        return rc, [s.as_dict() for s in sts]
+
+    def dbicgstab_oneshot(self, B, X, V=None, k: int = 0, U=None, tol: float = 1e-10,
+                          max_iter: int = 100000, stream=None):
+        nrhs = self._nrhs(B)
+        sts = (WdStats * nrhs)()
+        rc = lib().dbicgstab_solve(
+            self._h, _ptr(B), _ptr(X), nrhs, _ptr(V) if V is not None else None,
+            _ptr(U) if U is not None else None, int(k), float(tol), int(max_iter), sts,
+            _stream(stream, B, X))
+        check(rc, allow=(_lib.WD_OK, _lib.WD_NOT_CONVERGED, _lib.WD_BREAKDOWN))
+        return rc, [s.as_dict() for s in sts]
+
+
+class Deflation:
+    """The Sec. 2 deflation space: V, U (default gamma5 V), W = A V, LU(U^dagger A V)."""
+
+    def __init__(self, op: WilsonOperator, V, k: int, U=None, stream=None):
+        self.op = op
+        self.k = int(k)
+        d = ctypes.c_void_p()
+        check(lib().wd_deflation_create(op._h, _ptr(V), _ptr(U) if U is not None else None,
+                                        self.k, ctypes.byref(d), _stream(stream, V)))
+        self._d = d
+
+    def close(self):
+        if getattr(self, "_d", None) is not None and self._d.value:
+            lib().wd_deflation_destroy(self._d)
+            self._d = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,448 @@
+// C ABI of libwd.so (declared in include/wd.h): argument checks, host-pointer
+// staging, handle and deflation-space lifetime, error reporting.
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "solvers.h"
+#include "wd_internal.h"
+
+namespace wd {
+
+static thread_local std::string g_last_error;
+
+int bad_alloc();
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+int cuda_fail(cudaError_t e, const char *what) {
+  set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+  return e == cudaErrorMemoryAllocation ? WD_OUT_OF_MEMORY : WD_CUDA_ERROR;
+}
+
+bool is_device_pointer(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static thread_local Profiler *g_prof = nullptr;
+Profiler *current_profiler() { return g_prof; }
+void set_current_profiler(Profiler *p) { g_prof = p; }
+
+cudaEvent_t Profiler::take() {
+  if (!spare.empty()) {
+    cudaEvent_t e = spare.back();
+    spare.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void Profiler::flush() {
+  for (const Rec &r : pending) {
+    float t = 0.f;
+    cudaEventSynchronize(r.b);
+    cudaEventElapsedTime(&t, r.a, r.b);
+    launches[r.cat] += 1;
+    ms[r.cat] += t;
+    spare.push_back(r.a);
+    spare.push_back(r.b);
+  }
+  pending.clear();
+}
+
+void Profiler::reset() {
+  flush();
+  for (int c = 0; c < PC_COUNT; ++c) {
+    launches[c] = 0;
+    ms[c] = 0.0;
+  }
+  if (d_sites) cudaMemset(d_sites, 0, sizeof(unsigned long long));
+}
+
+void Profiler::destroy() {
+  flush();
+  for (cudaEvent_t e : spare) cudaEventDestroy(e);
+  spare.clear();
+  if (d_sites) cudaFree(d_sites);
+  d_sites = nullptr;
+}
+
+static int bad(const std::string &msg) {
+  set_error(msg);
+  return WD_BAD_ARG;
+}
+
+// A device view of a "device or host" vector argument.
+struct Staged {
+  double2 *dev = nullptr;
+  const void *user = nullptr;
+  bool host = false;
+  size_t bytes = 0;
+};
+
+static int stage_in(const void *user, size_t bytes, bool copy, Staged &st, Arena &ar,
+                    cudaStream_t s) {
+  st.user = user;
+  st.bytes = bytes;
+  st.host = !is_device_pointer(user);
+  if (!st.host) {
+    st.dev = const_cast<double2 *>(static_cast<const double2 *>(user));
+    return WD_OK;
+  }
+  st.dev = ar.take<double2>(bytes / sizeof(double2));
+  if (ar.failed) return bad_alloc();
+  if (copy) WD_CK(cudaMemcpyAsync(st.dev, user, bytes, cudaMemcpyHostToDevice, s));
+  return WD_OK;
+}
+
+}  // namespace wd
+
+namespace wd {
+int bad_alloc() {
+  set_error("out of device memory for solver scratch");
+  return WD_OUT_OF_MEMORY;
+}
+}  // namespace wd
+
+using namespace wd;
+
+// ------------------------------------------------------------------ handles
+
+extern "C" int wd_create(const int lat[4], const void *links, double kappa, double mu,
+                         wd_handle *out) {
+  if (out == nullptr) return bad("wd_create: out is NULL");
+  *out = nullptr;
+  if (lat == nullptr || links == nullptr) return bad("wd_create: lat or links is NULL");
+  long long V = 1;
+  for (int i = 0; i < 4; ++i) {
+    if (lat[i] < 1 || lat[i] > 4096) return bad("wd_create: lattice extents must be in [1, 4096]");
+    V *= lat[i];
+  }
+  if (V * 12 >= (1LL << 40)) return bad("wd_create: lattice too large");
+  wd_context *h = new wd_context();
+  h->prof.d_sites = nullptr;
+  for (int i = 0; i < 4; ++i) h->dims[i] = lat[i];
+  h->V = V;
+  h->n = 12 * V;
+  h->kappa = kappa;
+  h->mu = mu;
+  h->links = nullptr;
+  h->pool = nullptr;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaMalloc(&h->links, sizeof(double2) * 36 * V);
+  if (e == cudaSuccess) e = cudaMalloc(&h->prof.d_sites, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(h->prof.d_sites, 0, sizeof(unsigned long long));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h->links, links, sizeof(double2) * 36 * V, cudaMemcpyDefault);
+  if (e == cudaSuccess) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = h->device;
+    e = cudaMemPoolCreate(&h->pool, &props);
+    if (e == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      e = cudaMemPoolSetAttribute(h->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  }
+  if (e != cudaSuccess) {
+    int rc = cuda_fail(e, "wd_create");
+    if (h->links) cudaFree(h->links);
+    if (h->pool) cudaMemPoolDestroy(h->pool);
+    h->prof.destroy();
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return WD_OK;
+}
+
+extern "C" int wd_set_params(wd_handle h, double kappa, double mu) {
+  if (h == nullptr) return bad("wd_set_params: NULL handle");
+  h->kappa = kappa;
+  h->mu = mu;
+  return WD_OK;
+}
+
+extern "C" void wd_destroy(wd_handle h) {
+  if (h == nullptr) return;
+  cudaDeviceSynchronize();
+  h->prof.destroy();
+  if (h->links) cudaFree(h->links);
+  if (h->pool) cudaMemPoolDestroy(h->pool);
+  delete h;
+}
+
+extern "C" int wd_profile_enable(wd_handle h, unsigned mask) {
+  if (h == nullptr) return bad("wd_profile_enable: NULL handle");
+  h->prof.reset();
+  h->prof.mask = mask & ((1u << PC_COUNT) - 1);
+  return WD_OK;
+}
+
+extern "C" int wd_profile_read(wd_handle h, wd_profile *out) {
+  if (h == nullptr || out == nullptr) return bad("wd_profile_read: NULL argument");
+  h->prof.flush();
+  for (int c = 0; c < PC_COUNT; ++c) {
+    out->launches[c] = h->prof.launches[c];
+    out->ms[c] = h->prof.ms[c];
+  }
+  unsigned long long sites = 0;
+  cudaError_t e = cudaMemcpy(&sites, h->prof.d_sites, sizeof(sites), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "wd_profile_read");
+  out->dslash_site_updates = (long long)sites;
+  return WD_OK;
+}
+
+extern "C" int wd_apply(wd_handle h, const void *in, void *out, int nrhs, int dagger,
+                        wd_stream stream) {
+  ProfScope prof_scope_(h ? &h->prof : nullptr);
+  if (h == nullptr) return bad("wd_apply: NULL handle");
+  if (in == nullptr || out == nullptr) return bad("wd_apply: NULL vector");
+  if (nrhs < 1 || nrhs > 65535) return bad("wd_apply: nrhs must be in [1, 65535]");
+  if (in == out) return bad("wd_apply: in and out must not alias");
+  if (!is_device_pointer(in) || !is_device_pointer(out))
+    return bad("wd_apply: in and out must be device pointers");
+  const char *a = static_cast<const char *>(in);
+  const char *b = static_cast<const char *>(out);
+  const size_t bytes = sizeof(double2) * (size_t)h->n * nrhs;
+  if (a < b + bytes && b < a + bytes) return bad("wd_apply: in and out overlap");
+  cudaError_t e = launch_wilson_f64(h, static_cast<const double2 *>(in),
+                                    static_cast<double2 *>(out), nrhs, dagger ? 1 : 0,
+                                    (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "wd_apply");
+  return WD_OK;
+}
+
+// ------------------------------------------------------------------ GMRES-DR
+
+extern "C" int gmresdr_solve(wd_handle h, const void *b, void *x, int m, int k, double tol,
+                             int max_mv, void *V_out, void *Hbar_out, void *theta_out,
+                             wd_stats *stats, wd_stream stream) {
+  ProfScope prof_scope_(h ? &h->prof : nullptr);
+  if (h == nullptr) return bad("gmresdr_solve: NULL handle");
+  if (b == nullptr || x == nullptr) return bad("gmresdr_solve: NULL b or x");
+  if (m < 1 || m > 80) return bad("gmresdr_solve: m must be in [1, 80]");
+  if (k < 0 || k >= m) return bad("gmresdr_solve: k must satisfy 0 <= k < m");
+  if ((long long)m > h->n) return bad("gmresdr_solve: m exceeds the vector length");
+  if (!(tol > 0.0)) return bad("gmresdr_solve: tol must be positive");
+  if (max_mv < m) return bad("gmresdr_solve: max_mv must be >= m");
+  if (V_out != nullptr && !is_device_pointer(V_out)) return bad("gmresdr_solve: V_out must be device memory");
+  cudaStream_t s = (cudaStream_t)stream;
+  Arena ar;
+  ar.pool = h->pool;
+  ar.stream = s;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  const size_t bytes = sizeof(double2) * (size_t)h->n;
+  Staged sb, sx;
+  int rc = stage_in(b, bytes, true, sb, ar, s);
+  if (rc == WD_OK) rc = stage_in(x, bytes, true, sx, ar, s);
+  wd_stats local;
+  std::memset(&local, 0, sizeof(local));
+  if (rc == WD_OK)
+    rc = gmresdr_run(h, sb.dev, sx.dev, m, k, tol, max_mv, static_cast<double2 *>(V_out),
+                     static_cast<double2 *>(Hbar_out), static_cast<double2 *>(theta_out),
+                     &local, s, nullptr, 0, ar);
+  if ((rc == WD_OK || rc == WD_NOT_CONVERGED) && sx.host) {
+    cudaError_t e = cudaMemcpyAsync(x, sx.dev, bytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "gmresdr_solve: copy x");
+  }
+  cudaEventRecord(e1, s);
+  ar.release();
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess && (rc == WD_OK || rc == WD_NOT_CONVERGED)) rc = cuda_fail(e, "gmresdr_solve");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  local.ms = ms;
+  if (stats) *stats = local;
+  return rc;
+}
+
+// ------------------------------------------------------------------ deflation
+
+extern "C" int wd_deflation_create(wd_handle h, const void *V, const void *U, int k,
+                                   wd_deflation *out, wd_stream stream) {
+  ProfScope prof_scope_(h ? &h->prof : nullptr);
+  if (out == nullptr) return bad("wd_deflation_create: out is NULL");
+  *out = nullptr;
+  if (h == nullptr || V == nullptr) return bad("wd_deflation_create: NULL handle or V");
+  if (k < 1 || k > 128) return bad("wd_deflation_create: k must be in [1, 128]");
+  if (!is_device_pointer(V) || (U != nullptr && !is_device_pointer(U)))
+    return bad("wd_deflation_create: V and U must be device memory");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t vb = sizeof(double2) * (size_t)h->n * k;
+  wd_deflation_space *d = new wd_deflation_space();
+  std::memset(d, 0, sizeof(*d));
+  d->h = h;
+  d->k = k;
+  d->kappa = h->kappa;
+  d->mu = h->mu;
+  cudaError_t e = cudaMalloc(&d->V, vb);
+  if (e == cudaSuccess && U) e = cudaMalloc(&d->U, vb);
+  if (e == cudaSuccess) e = cudaMalloc(&d->W, vb);
+  if (e == cudaSuccess) e = cudaMalloc(&d->LU, sizeof(double2) * k * k);
+  if (e == cudaSuccess) e = cudaMalloc(&d->piv, sizeof(int) * k);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d->V, V, vb, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && U) e = cudaMemcpyAsync(d->U, U, vb, cudaMemcpyDeviceToDevice, s);
+  int rc = e == cudaSuccess ? WD_OK : cuda_fail(e, "wd_deflation_create");
+  if (rc == WD_OK) {
+    Arena ar;
+    ar.pool = h->pool;
+    ar.stream = s;
+    rc = deflation_build(d, s, ar);
+    ar.release();
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    if (rc == WD_OK && e2 != cudaSuccess) rc = cuda_fail(e2, "wd_deflation_create");
+  }
+  if (rc != WD_OK) {
+    wd_deflation_destroy(d);
+    return rc;
+  }
+  *out = d;
+  return WD_OK;
+}
+
+extern "C" void wd_deflation_destroy(wd_deflation d) {
+  if (d == nullptr) return;
+  cudaDeviceSynchronize();
+  cudaFree(d->V);
+  cudaFree(d->U);
+  cudaFree(d->W);
+  cudaFree(d->LU);
+  cudaFree(d->piv);
+  delete d;
+}
+
+// ------------------------------------------------------------------ D-BiCGStab
+
+extern "C" int dbicgstab_solve_deflated(wd_handle h, wd_deflation d, const void *B, void *X,
+                                        int nrhs, double tol, int max_iter, wd_stats *stats,
+                                        wd_stream stream) {
+  ProfScope prof_scope_(h ? &h->prof : nullptr);
+  if (h == nullptr) return bad("dbicgstab_solve: NULL handle");
+  if (B == nullptr || X == nullptr) return bad("dbicgstab_solve: NULL B or X");
+  if (nrhs < 1 || nrhs > 65535) return bad("dbicgstab_solve: nrhs must be in [1, 65535]");
+  if (!(tol > 0.0)) return bad("dbicgstab_solve: tol must be positive");
+  if (max_iter < 1) return bad("dbicgstab_solve: max_iter must be >= 1");
+  if (d != nullptr && d->h != h) return bad("dbicgstab_solve: deflation space built for another handle");
+  if (d != nullptr && (d->kappa != h->kappa || d->mu != h->mu))
+    return bad("dbicgstab_solve: kappa/mu changed since the deflation space was built");
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long n = h->n;
+  Arena ar;
+  ar.pool = h->pool;
+  ar.stream = s;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  const size_t bytes = sizeof(double2) * (size_t)n * nrhs;
+  Staged sb, sx;
+  std::vector<wd_stats> local(nrhs);
+  std::memset(local.data(), 0, sizeof(wd_stats) * nrhs);
+  int rc = stage_in(B, bytes, true, sb, ar, s);
+  if (rc == WD_OK) rc = stage_in(X, bytes, true, sx, ar, s);
+  double2 *R0 = rc == WD_OK ? ar.take<double2>((size_t)n * nrhs) : nullptr;
+  double *part = rc == WD_OK ? ar.take<double>((size_t)stream_blocks(n) * 2 * nrhs) : nullptr;
+  if (rc == WD_OK && ar.failed) rc = bad_alloc();
+  if (rc == WD_OK) {
+    // r0 = B - A X0, skipping the product when every X0 is zero (the usual x0 = 0)
+    std::vector<double> hp((size_t)stream_blocks(n) * 2 * nrhs);
+    cudaError_t e = launch_norms(sx.dev, nullptr, part, n, nrhs, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hp.data(), part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "dbicgstab_solve: ||x0||");
+    bool zero = true;
+    for (size_t i = 0; i < hp.size(); i += 2) zero &= hp[i] == 0.0;
+    if (rc == WD_OK) {
+      if (zero) {
+        e = cudaMemcpyAsync(R0, sb.dev, bytes, cudaMemcpyDeviceToDevice, s);
+      } else {
+        e = launch_wilson_f64(h, sx.dev, R0, nrhs, 0, s);
+        if (e == cudaSuccess) e = launch_sub_norm(R0, sb.dev, R0, nullptr, M_ALL, part, n, nrhs, s);
+        for (auto &q : local) q.mvp_extra += 1;
+      }
+      if (e != cudaSuccess) rc = cuda_fail(e, "dbicgstab_solve: r0");
+    }
+  }
+  if (rc == WD_OK && d != nullptr) rc = deflate_batched(d, sx.dev, R0, nrhs, s, ar);
+  if (rc == WD_OK)
+    rc = bicgstab_batched(h, sb.dev, sx.dev, R0, nrhs, tol, max_iter, local.data(), s, nullptr,
+                          0, ar);
+  if ((rc == WD_OK || rc == WD_NOT_CONVERGED || rc == WD_BREAKDOWN) && sx.host) {
+    cudaError_t e = cudaMemcpyAsync(X, sx.dev, bytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "dbicgstab_solve: copy X");
+  }
+  cudaEventRecord(e1, s);
+  ar.release();
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess && rc != WD_CUDA_ERROR) rc = cuda_fail(e, "dbicgstab_solve");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (stats) {
+    for (int q = 0; q < nrhs; ++q) {
+      local[q].ms = ms;
+      stats[q] = local[q];
+    }
+  }
+  return rc;
+}
+
+extern "C" int dbicgstab_solve(wd_handle h, const void *B, void *X, int nrhs, const void *V,
+                               const void *U, int k, double tol, int max_iter, wd_stats *stats,
+                               wd_stream stream) {
+  if (h == nullptr) return bad("dbicgstab_solve: NULL handle");
+  if (k < 0) return bad("dbicgstab_solve: k must be >= 0");
+  if (k > 0 && V == nullptr) return bad("dbicgstab_solve: V is NULL with k > 0");
+  wd_deflation d = nullptr;
+  if (k > 0) {
+    int rc = wd_deflation_create(h, V, U, k, &d, stream);
+    if (rc != WD_OK) return rc;
+  }
+  int rc = dbicgstab_solve_deflated(h, d, B, X, nrhs, tol, max_iter, stats, stream);
+  if (d) wd_deflation_destroy(d);
+  return rc;
+}
+
+// ------------------------------------------------------------------ errors
+
+extern "C" const char *wd_error_string(int status) {
+  switch (status) {
+    case WD_OK: return "ok";
+    case WD_BAD_ARG: return "invalid argument";
+    case WD_NOT_CONVERGED: return "not converged";
+    case WD_BREAKDOWN: return "Krylov breakdown";
+    case WD_SINGULAR_PROJECTION: return "singular projected matrix";
+    case WD_TIMEOUT: return "device-side wait timed out";
+    case WD_CUDA_ERROR: return "CUDA error";
+    case WD_OUT_OF_MEMORY: return "out of device memory";
+    default: return "unknown status";
+  }
+}
+
+extern "C" int wd_last_error_detail(char *buf, size_t len) {
+  const std::string &m = g_last_error;
+  if (buf != nullptr && len > 0) {
+    size_t c = m.size() < len - 1 ? m.size() : len - 1;
+    std::memcpy(buf, m.data(), c);
+    buf[c] = '\0';
+  }
+  return (int)m.size();
+}

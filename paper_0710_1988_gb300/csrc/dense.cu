@@ -1,0 +1,616 @@
+// Small dense FP64 complex linear algebra on one thread block.
+//
+//  * LU with partial pivoting and triangular solves: the k x k projected
+//    system (U^dagger A V) y = U^dagger r0 of Sec. 2.
+//  * The end of a GMRES-DR(m,k) cycle (Morgan's deflated restarting, cited
+//    in Sec. 1): least squares min ||c - Hbar d|| by Householder QR, the
+//    harmonic Ritz pairs of H_m + |h_{m+1,m}|^2 f e_m^T (f = H_m^{-dagger}
+//    e_m) by Householder reduction to Hessenberg form and complex shifted
+//    QR iteration (Schur form, then eigenvectors by back substitution),
+//    selection of the k smallest |theta|, the orthonormal P_{k+1}, and the
+//    restarted Hbar_k = P_{k+1}^dagger Hbar_m P_k, c = P_{k+1}^dagger rho.
+//
+// Matrices are small (m <= 80, k <= 128); these kernels run one CTA and
+// keep their working matrices in shared memory.  Every loop is bounded.
+#include "cplx.cuh"
+#include "kernels.cuh"
+#include "wd_internal.h"
+
+namespace wd {
+
+constexpr int LU_THREADS = 256;
+constexpr int CE_THREADS = 512;
+constexpr int CE_MAXM = 80;
+
+__device__ __forceinline__ double cabs1(double2 a) { return fabs(a.x) + fabs(a.y); }
+
+__device__ double2 csqrt_(double2 z) {
+  const double r = hypot(z.x, z.y);
+  if (r == 0.0) return make_double2(0.0, 0.0);
+  const double w = sqrt(0.5 * (r + fabs(z.x)));
+  if (z.x >= 0.0) return make_double2(w, z.y / (2.0 * w));
+  return make_double2(fabs(z.y) / (2.0 * w), copysign(w, z.y));
+}
+
+// Block-wide argmax of (val, idx); ties go to the smaller index.  Result in
+// every thread.  blockDim.x multiple of 32, <= 1024.
+__device__ void block_argmax(double &val, int &idx) {
+  __shared__ double sv[32];
+  __shared__ int si[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ov = __shfl_down_sync(0xffffffffu, val, off);
+    const int oi = __shfl_down_sync(0xffffffffu, idx, off);
+    if (ov > val || (ov == val && oi < idx)) {
+      val = ov;
+      idx = oi;
+    }
+  }
+  __syncthreads();
+  if (lane == 0) {
+    sv[w] = val;
+    si[w] = idx;
+  }
+  __syncthreads();
+  if (w == 0) {
+    val = lane < nw ? sv[lane] : -1.0;
+    idx = lane < nw ? si[lane] : 0x7fffffff;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const double ov = __shfl_down_sync(0xffffffffu, val, off);
+      const int oi = __shfl_down_sync(0xffffffffu, idx, off);
+      if (ov > val || (ov == val && oi < idx)) {
+        val = ov;
+        idx = oi;
+      }
+    }
+    if (lane == 0) {
+      sv[0] = val;
+      si[0] = idx;
+    }
+  }
+  __syncthreads();
+  val = sv[0];
+  idx = si[0];
+  __syncthreads();
+}
+
+// Sum of a complex value over the block, result in every thread.
+__device__ double2 block_csum_all(double2 v) {
+  __shared__ double2 res;
+  double t[2] = {v.x, v.y};
+  block_sum<2>(t);
+  if (threadIdx.x == 0) res = make_double2(t[0], t[1]);
+  __syncthreads();
+  const double2 r = res;
+  __syncthreads();
+  return r;
+}
+
+__device__ double block_dsum_all(double v) {
+  __shared__ double res;
+  double t[1] = {v};
+  block_sum<1>(t);
+  if (threadIdx.x == 0) res = t[0];
+  __syncthreads();
+  const double r = res;
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ double2 warp_csum_all(double2 v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
+  }
+  return v;
+}
+
+// In-place LU with partial pivoting of the k x k matrix A (leading dim ld).
+// Returns 1 if an exactly zero pivot was met.  Every thread of the block calls it.
+__device__ int lu_factor_block(double2 *A, int ld, int k, int *piv) {
+  int singular = 0;
+  for (int j = 0; j < k; ++j) {
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    for (int i = j + threadIdx.x; i < k; i += blockDim.x) {
+      const double v = cabs_(A[i * ld + j]);
+      if (v > best || (v == best && i < bi)) {
+        best = v;
+        bi = i;
+      }
+    }
+    block_argmax(best, bi);
+    const int p = bi;
+    if (threadIdx.x == 0) piv[j] = p;
+    if (p != j) {
+      for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        const double2 t = A[j * ld + c];
+        A[j * ld + c] = A[p * ld + c];
+        A[p * ld + c] = t;
+      }
+    }
+    __syncthreads();
+    const double2 pv = A[j * ld + j];
+    if (pv.x == 0.0 && pv.y == 0.0) {
+      singular = 1;
+      continue;
+    }
+    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) A[i * ld + j] = cdiv(A[i * ld + j], pv);
+    __syncthreads();
+    const int w = k - j - 1;
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+      const int i = j + 1 + e / w, c = j + 1 + e % w;
+      A[i * ld + c] = csub(A[i * ld + c], cmul(A[i * ld + j], A[j * ld + c]));
+    }
+    __syncthreads();
+  }
+  return singular;
+}
+
+// Solve (LU) Y = C in place for nrhs columns of C (row-major, leading dim ldc).
+__device__ void lu_solve_block(const double2 *LU, int ld, const int *piv, int k, double2 *C,
+                               int ldc, int nrhs) {
+  for (int r = threadIdx.x; r < nrhs; r += blockDim.x) {
+    for (int j = 0; j < k; ++j) {
+      const int p = piv[j];
+      if (p != j) {
+        const double2 t = C[j * ldc + r];
+        C[j * ldc + r] = C[p * ldc + r];
+        C[p * ldc + r] = t;
+      }
+    }
+  }
+  __syncthreads();
+  for (int j = 0; j < k; ++j) {  // unit lower triangle
+    const int w = k - j - 1;
+    for (int e = threadIdx.x; e < w * nrhs; e += blockDim.x) {
+      const int i = j + 1 + e / nrhs, r = e % nrhs;
+      C[i * ldc + r] = csub(C[i * ldc + r], cmul(LU[i * ld + j], C[j * ldc + r]));
+    }
+    __syncthreads();
+  }
+  for (int j = k - 1; j >= 0; --j) {  // upper triangle
+    const double2 u = LU[j * ld + j];
+    for (int r = threadIdx.x; r < nrhs; r += blockDim.x) {
+      const double2 v = C[j * ldc + r];
+      C[j * ldc + r] = (u.x == 0.0 && u.y == 0.0) ? make_double2(0.0, 0.0) : cdiv(v, u);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < j * nrhs; e += blockDim.x) {
+      const int i = e / nrhs, r = e % nrhs;
+      C[i * ldc + r] = csub(C[i * ldc + r], cmul(LU[i * ld + j], C[j * ldc + r]));
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(LU_THREADS)
+lu_factor_kernel(double2 *A, int k, int *piv, double *info) {
+  const int sing = lu_factor_block(A, k, k, piv);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mx = 0.0, mn = 1e308;
+    for (int j = 0; j < k; ++j) {
+      const double v = cabs_(A[j * k + j]);
+      mx = fmax(mx, v);
+      mn = fmin(mn, v);
+    }
+    info[0] = sing ? 1.0 : 0.0;
+    info[1] = mn > 0.0 ? mx / mn : 1e308;  // crude condition estimate from the pivots
+  }
+}
+
+__global__ void __launch_bounds__(LU_THREADS)
+lu_solve_kernel(const double2 *LU, const int *piv, int k, double2 *C, int nrhs) {
+  lu_solve_block(LU, k, piv, k, C, nrhs, nrhs);
+}
+
+cudaError_t launch_lu_factor(double2 *A, int k, int *piv, double *info, cudaStream_t s) {
+  ProfLaunch prof_(PC_DENSE, s);
+  lu_factor_kernel<<<1, LU_THREADS, 0, s>>>(A, k, piv, info);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lu_solve(const double2 *LU, const int *piv, int k, double2 *C, int nrhs,
+                            cudaStream_t s) {
+  ProfLaunch prof_(PC_DENSE, s);
+  lu_solve_kernel<<<1, LU_THREADS, 0, s>>>(LU, piv, k, C, nrhs);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- GMRES-DR cycle end
+
+// Apply the Householder reflector I - tau u u^dagger (u[i] for i >= i0) from
+// the left to columns [c0, c1) of X (rows i0..i1, leading dim ld), one warp
+// per column.
+__device__ void reflect_left(double2 *X, int ld, const double2 *u, double tau, int i0, int i1,
+                             int c0, int c1) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = c0 + w; c < c1; c += nw) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int i = i0 + lane; i <= i1; i += 32) s = cfmac(u[i], X[i * ld + c], s);
+    s = warp_csum_all(s);
+    const double2 f = cscale(tau, s);
+    for (int i = i0 + lane; i <= i1; i += 32) X[i * ld + c] = csub(X[i * ld + c], cmul(u[i], f));
+  }
+}
+
+// ... and from the right to rows [r0, r1) of X (columns i0..i1).
+__device__ void reflect_right(double2 *X, int ld, const double2 *u, double tau, int i0, int i1,
+                              int r0, int r1) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r = r0 + w; r < r1; r += nw) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int i = i0 + lane; i <= i1; i += 32) s = cfma(X[r * ld + i], u[i], s);
+    s = warp_csum_all(s);
+    const double2 f = cscale(tau, s);
+    for (int i = i0 + lane; i <= i1; i += 32)
+      X[r * ld + i] = csub(X[r * ld + i], cmul(f, cconj(u[i])));
+  }
+}
+
+// Least squares min || c - Hbar d || for the (me+1) x me leading part of the
+// row-major (m+1) x m Hbar.  Writes d (m entries, zero beyond me), rho = c - Hbar d
+// (m+1 entries) and ||rho||.
+__device__ void cycle_lsq(const CycleEndArgs &a, int me, double2 *sm) {
+  const int m = a.m, ld = m;
+  double2 *Hs = sm;                    // (m+1) x m
+  double2 *cz = Hs + (m + 1) * m;      // m+1
+  double2 *u = cz + (m + 1);           // m+1
+  double2 *dd = u + (m + 1);           // m
+  for (int e = threadIdx.x; e < (m + 1) * m; e += blockDim.x) Hs[e] = a.H[e];
+  for (int i = threadIdx.x; i <= m; i += blockDim.x) cz[i] = a.c[i];
+  __syncthreads();
+  for (int j = 0; j < me; ++j) {
+    double part = 0.0;
+    for (int i = j + threadIdx.x; i <= me; i += blockDim.x) part += cnorm2(Hs[i * ld + j]);
+    const double sigma = block_dsum_all(part);
+    if (sigma == 0.0) continue;
+    const double2 al = Hs[j * ld + j];
+    const double nx = sqrt(sigma), aa = cabs_(al);
+    const double2 ph = aa > 0.0 ? cscale(1.0 / aa, al) : make_double2(1.0, 0.0);
+    const double2 beta = cscale(-nx, ph);
+    for (int i = j + threadIdx.x; i <= me; i += blockDim.x)
+      u[i] = i == j ? csub(al, beta) : Hs[i * ld + j];
+    __syncthreads();
+    const double tau = 1.0 / (nx * (nx + aa));  // 2 / ||u||^2
+    reflect_left(Hs, ld, u, tau, j, me, j + 1, me);
+    reflect_left(cz, 1, u, tau, j, me, 0, 1);
+    __syncthreads();
+    for (int i = j + threadIdx.x; i <= me; i += blockDim.x)
+      Hs[i * ld + j] = i == j ? beta : make_double2(0.0, 0.0);
+    __syncthreads();
+  }
+  for (int j = me - 1; j >= 0; --j) {
+    if (threadIdx.x == 0) {
+      const double2 rjj = Hs[j * ld + j];
+      dd[j] = (rjj.x == 0.0 && rjj.y == 0.0) ? make_double2(0.0, 0.0) : cdiv(cz[j], rjj);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < j; i += blockDim.x) cz[i] = csub(cz[i], cmul(Hs[i * ld + j], dd[j]));
+    __syncthreads();
+  }
+  for (int j = threadIdx.x; j < m; j += blockDim.x) a.d[j] = j < me ? dd[j] : make_double2(0.0, 0.0);
+  double part = 0.0;
+  for (int i = threadIdx.x; i <= m; i += blockDim.x) {
+    double2 v = a.c[i];
+    for (int j = 0; j < me; ++j) v = csub(v, cmul(a.H[i * ld + j], dd[j]));
+    a.rho[i] = v;
+    part += cnorm2(v);
+  }
+  const double rr = block_dsum_all(part);
+  if (threadIdx.x == 0) a.res[0] = sqrt(rr);
+  __syncthreads();
+}
+
+// Complex Givens rotation G = [[c, s], [-conj(s), c]] with G [x; y] = [r; 0].
+__device__ __forceinline__ void givens(double2 x, double2 y, double &c, double2 &s) {
+  const double ax = cabs_(x);
+  if (ax == 0.0) {
+    c = 0.0;
+    s = make_double2(1.0, 0.0);
+    return;
+  }
+  const double nrm = hypot(ax, cabs_(y));
+  c = ax / nrm;
+  s = cscale(1.0 / (ax * nrm), cmul(x, cconj(y)));
+}
+
+// Schur decomposition of the m x m matrix A (smem, row-major): on return
+// A holds upper triangular T and Z the unitary Schur vectors, A_in = Z T Z^dagger.
+// Returns 1 if the QR iteration did not converge in 30 m sweeps.
+__device__ int schur_block(double2 *A, double2 *Z, int m, double2 *u) {
+  const int tid = threadIdx.x, bd = blockDim.x;
+  for (int e = tid; e < m * m; e += bd)
+    Z[e] = (e / m == e % m) ? make_double2(1.0, 0.0) : make_double2(0.0, 0.0);
+  __syncthreads();
+  // Householder reduction to upper Hessenberg form
+  for (int j = 0; j + 2 < m; ++j) {
+    double part = 0.0;
+    for (int i = j + 2 + tid; i < m; i += bd) part += cnorm2(A[i * m + j]);
+    const double below = block_dsum_all(part);
+    if (below == 0.0) continue;
+    const double2 al = A[(j + 1) * m + j];
+    const double aa = cabs_(al), nx = sqrt(below + aa * aa);
+    const double2 ph = aa > 0.0 ? cscale(1.0 / aa, al) : make_double2(1.0, 0.0);
+    const double2 beta = cscale(-nx, ph);
+    for (int i = j + 1 + tid; i < m; i += bd) u[i] = i == j + 1 ? csub(al, beta) : A[i * m + j];
+    __syncthreads();
+    const double tau = 1.0 / (nx * (nx + aa));
+    reflect_left(A, m, u, tau, j + 1, m - 1, j, m);
+    __syncthreads();
+    reflect_right(A, m, u, tau, j + 1, m - 1, 0, m);
+    reflect_right(Z, m, u, tau, j + 1, m - 1, 0, m);
+    __syncthreads();
+    for (int i = j + 1 + tid; i < m; i += bd)
+      A[i * m + j] = i == j + 1 ? beta : make_double2(0.0, 0.0);
+    __syncthreads();
+  }
+  double part = 0.0;
+  for (int e = tid; e < m * m; e += bd) part = fmax(part, cabs1(A[e]));
+  {
+    __shared__ double smax[32];
+    for (int off = 16; off > 0; off >>= 1) part = fmax(part, __shfl_down_sync(0xffffffffu, part, off));
+    if ((tid & 31) == 0) smax[tid >> 5] = part;
+    __syncthreads();
+    if (tid == 0) {
+      double mx = 0.0;
+      for (int w = 0; w < (bd >> 5); ++w) mx = fmax(mx, smax[w]);
+      smax[0] = mx;
+    }
+    __syncthreads();
+    part = smax[0];
+    __syncthreads();
+  }
+  const double anorm = part > 0.0 ? part : 1.0;
+  // shifted QR iteration
+  int hi = m - 1, its = 0, total = 0;
+  while (hi > 0) {
+    if (total >= 30 * m) return 1;
+    int l = hi;
+    for (; l > 0; --l) {
+      double tst = cabs1(A[(l - 1) * m + l - 1]) + cabs1(A[l * m + l]);
+      if (tst == 0.0) tst = anorm;
+      if (cabs1(A[l * m + l - 1]) <= 2.220446049250313e-16 * tst) break;
+    }
+    __syncthreads();
+    if (l > 0 && tid == 0) A[l * m + l - 1] = make_double2(0.0, 0.0);
+    __syncthreads();
+    if (l == hi) {
+      --hi;
+      its = 0;
+      continue;
+    }
+    ++its;
+    ++total;
+    const double2 a = A[(hi - 1) * m + hi - 1], b = A[(hi - 1) * m + hi];
+    const double2 c = A[hi * m + hi - 1], d = A[hi * m + hi];
+    double2 sigma;
+    if (its % 10 == 0) {
+      sigma = cadd(d, make_double2(cabs1(c), 0.0));  // exceptional shift
+    } else {  // eigenvalue of the trailing 2x2 block nearest to d
+      const double2 p = cscale(0.5, csub(a, d));
+      const double2 bc = cmul(b, c);
+      double2 q = csqrt_(cadd(cmul(p, p), bc));
+      if (p.x * q.x + p.y * q.y < 0.0) q = cneg(q);
+      const double2 den = cadd(p, q);
+      sigma = (den.x == 0.0 && den.y == 0.0) ? d : csub(d, cdiv(bc, den));
+    }
+    double2 x = csub(A[l * m + l], sigma), y = A[(l + 1) * m + l];
+    __syncthreads();
+    for (int kk = l; kk < hi; ++kk) {
+      double gc;
+      double2 gs;
+      givens(x, y, gc, gs);
+      const double2 mgs = cneg(cconj(gs));
+      const int c0 = kk > l ? kk - 1 : l;
+      for (int j = c0 + tid; j < m; j += bd) {
+        const double2 a1 = A[kk * m + j], a2 = A[(kk + 1) * m + j];
+        A[kk * m + j] = cadd(cscale(gc, a1), cmul(gs, a2));
+        A[(kk + 1) * m + j] = (kk > l && j == kk - 1) ? make_double2(0.0, 0.0)
+                                                       : cadd(cmul(mgs, a1), cscale(gc, a2));
+      }
+      __syncthreads();
+      const int rmax = kk + 2 < hi ? kk + 2 : hi;
+      const double2 cgs = cconj(gs), ngs = cneg(gs);
+      for (int i = tid; i < rmax + 1 + m; i += bd) {
+        double2 *X = i <= rmax ? A : Z;
+        const int row = i <= rmax ? i : i - rmax - 1;
+        const double2 a1 = X[row * m + kk], a2 = X[row * m + kk + 1];
+        X[row * m + kk] = cadd(cscale(gc, a1), cmul(cgs, a2));
+        X[row * m + kk + 1] = cadd(cmul(ngs, a1), cscale(gc, a2));
+      }
+      __syncthreads();
+      if (kk < hi - 1) {
+        x = A[(kk + 1) * m + kk];
+        y = A[(kk + 2) * m + kk];
+      }
+      __syncthreads();
+    }
+  }
+  return 0;
+}
+
+__global__ void __launch_bounds__(CE_THREADS) gmresdr_cycle_end_kernel(CycleEndArgs a) {
+  extern __shared__ double2 sm[];
+  __shared__ int sel[CE_MAXM];
+  __shared__ int piv[CE_MAXM];
+  const int m = a.m, k = a.k, tid = threadIdx.x, bd = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = bd >> 5;
+  const int me = *a.m_eff;
+  if (tid == 0) {
+    a.flags[0] = 0;
+    a.flags[1] = me < m ? 1 : 0;
+  }
+  cycle_lsq(a, me, sm);
+  if (!a.do_restart || me < m) return;
+  const double res = a.res[0];
+  double2 *P = a.P;
+  const int ldp = k + 1;
+  if (k == 0) {  // plain GMRES(m) restart: v_1 = V_{m+1} rho / ||rho||
+    for (int i = tid; i <= m; i += bd)
+      P[i] = res > 0.0 ? cscale(1.0 / res, a.rho[i]) : make_double2(0.0, 0.0);
+    if (tid == 0) a.ck[0] = make_double2(res, 0.0);
+    return;
+  }
+  double2 *A = sm;               // m x m
+  double2 *Z = A + m * m;        // m x m
+  double2 *v1 = Z + m * m;       // m+1
+  double2 *v2 = v1 + (m + 1);    // m+1
+  // harmonic Ritz matrix H_m + |h_{m+1,m}|^2 f e_m^T with H_m^dagger f = e_m
+  for (int e = tid; e < m * m; e += bd) {
+    const int i = e / m, j = e % m;
+    A[e] = a.H[i * m + j];
+    Z[j * m + i] = cconj(a.H[i * m + j]);
+  }
+  for (int i = tid; i < m; i += bd) v1[i] = make_double2(i == m - 1 ? 1.0 : 0.0, 0.0);
+  __syncthreads();
+  lu_factor_block(Z, m, m, piv);
+  __syncthreads();
+  lu_solve_block(Z, m, piv, m, v1, 1, 1);
+  const double hh = cnorm2(a.H[m * m + m - 1]);
+  for (int i = tid; i < m; i += bd) A[i * m + m - 1] = cadd(A[i * m + m - 1], cscale(hh, v1[i]));
+  __syncthreads();
+  if (schur_block(A, Z, m, v2)) {
+    if (tid == 0) a.flags[0] = 1;
+    return;
+  }
+  __syncthreads();
+  // order eigenvalues by (|theta|, Re, Im), index as the final tie-break
+  for (int i = tid; i < m; i += bd) {
+    const double2 ti = A[i * m + i];
+    const double ai = cabs_(ti);
+    int rank = 0;
+    for (int j = 0; j < m; ++j) {
+      const double2 tj = A[j * m + j];
+      const double aj = cabs_(tj);
+      const bool less = aj < ai || (aj == ai && (tj.x < ti.x || (tj.x == ti.x && (tj.y < ti.y ||
+                                                   (tj.y == ti.y && j < i)))));
+      rank += less ? 1 : 0;
+    }
+    if (rank < k) sel[rank] = i;
+  }
+  __syncthreads();
+  // eigenvectors of T by back substitution, one warp per selected value;
+  // g = Z y written to G (m x k, row-major) in the work buffer
+  double2 *G = a.work;
+  for (int q = wid; q < k; q += nw) {
+    const int i = sel[q];
+    const double2 lam = A[i * m + i];
+    double2 rhs[3], y[3];  // rows lane, lane+32, lane+64
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      const int row = lane + 32 * t;
+      rhs[t] = row < i ? cneg(A[row * m + i]) : make_double2(0.0, 0.0);
+      y[t] = row == i ? make_double2(1.0, 0.0) : make_double2(0.0, 0.0);
+    }
+    const double smin = fmax(2.220446049250313e-16 * (cabs1(lam) + 1e-300), 1e-290);
+    for (int j = i - 1; j >= 0; --j) {
+      const int own = j & 31, slot = j >> 5;
+      double2 yj = make_double2(0.0, 0.0);
+      if (lane == own) {
+        double2 den = csub(A[j * m + j], lam);
+        if (cabs1(den) < smin) den = make_double2(smin, 0.0);
+        const double2 r = slot == 0 ? rhs[0] : (slot == 1 ? rhs[1] : rhs[2]);
+        yj = cdiv(r, den);
+        if (slot == 0) y[0] = yj;
+        else if (slot == 1) y[1] = yj;
+        else y[2] = yj;
+      }
+      yj.x = __shfl_sync(0xffffffffu, yj.x, own);
+      yj.y = __shfl_sync(0xffffffffu, yj.y, own);
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        const int row = lane + 32 * t;
+        if (row < j) rhs[t] = csub(rhs[t], cmul(A[row * m + j], yj));
+      }
+    }
+    // g = Z y
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      const int row = lane + 32 * t;
+      double2 g = make_double2(0.0, 0.0);
+      for (int j = 0; j <= i; ++j) {
+        const int own = j & 31, slot = j >> 5;
+        double2 yj = slot == 0 ? y[0] : (slot == 1 ? y[1] : y[2]);
+        yj.x = __shfl_sync(0xffffffffu, yj.x, own);
+        yj.y = __shfl_sync(0xffffffffu, yj.y, own);
+        if (row < m) g = cfma(Z[row * m + j], yj, g);
+      }
+      if (row < m) G[row * k + q] = g;
+    }
+  }
+  __syncthreads();
+  // P_k = QR of [g_1..g_k; 0] by Gram-Schmidt applied twice; p_{k+1} from rho
+  double2 *coef = v2;
+  for (int c = 0; c <= k; ++c) {
+    for (int i = tid; i <= m; i += bd)
+      v1[i] = c < k ? (i < m ? G[i * k + c] : make_double2(0.0, 0.0)) : a.rho[i];
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int j = wid; j < c; j += nw) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int i = lane; i <= m; i += 32) s = cfmac(P[i * ldp + j], v1[i], s);
+        s = warp_csum_all(s);
+        if (lane == 0) coef[j] = s;
+      }
+      __syncthreads();
+      for (int i = tid; i <= m; i += bd) {
+        double2 v = v1[i];
+        for (int j = 0; j < c; ++j) v = csub(v, cmul(P[i * ldp + j], coef[j]));
+        v1[i] = v;
+      }
+      __syncthreads();
+    }
+    double part2 = 0.0;
+    for (int i = tid; i <= m; i += bd) part2 += cnorm2(v1[i]);
+    const double nv = sqrt(block_dsum_all(part2));
+    if (nv == 0.0 && tid == 0) a.flags[0] = 2;
+    for (int i = tid; i <= m; i += bd) P[i * ldp + c] = nv > 0.0 ? cscale(1.0 / nv, v1[i]) : v1[i];
+    __syncthreads();
+  }
+  // T1 = Hbar_m P_k ((m+1) x k) in the work buffer, then Hk = P^dagger T1, ck = P^dagger rho
+  double2 *T1 = a.work + (size_t)m * k;
+  for (int e = tid; e < (m + 1) * k; e += bd) {
+    const int i = e / k, b = e % k;
+    double2 s = make_double2(0.0, 0.0);
+    for (int l = 0; l < m; ++l) s = cfma(a.H[i * m + l], P[l * ldp + b], s);
+    T1[e] = s;
+  }
+  __syncthreads();
+  for (int e = tid; e < (k + 1) * k; e += bd) {
+    const int r = e / k, b = e % k;
+    double2 s = make_double2(0.0, 0.0);
+    for (int i = 0; i <= m; ++i) s = cfmac(P[i * ldp + r], T1[i * k + b], s);
+    a.Hk[e] = s;
+  }
+  for (int r = tid; r <= k; r += bd) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int i = 0; i <= m; ++i) s = cfmac(P[i * ldp + r], a.rho[i], s);
+    a.ck[r] = s;
+  }
+  for (int q = tid; q < k; q += bd) a.theta[q] = A[sel[q] * m + sel[q]];
+}
+
+size_t gmresdr_cycle_end_smem(int m) {
+  const size_t lsq = (size_t)(m + 1) * m + 3 * (m + 1);
+  const size_t eig = (size_t)2 * m * m + 2 * (m + 1);
+  return (lsq > eig ? lsq : eig) * sizeof(double2);
+}
+
+cudaError_t launch_gmresdr_cycle_end(const CycleEndArgs &a, cudaStream_t s) {
+  ProfLaunch prof_(PC_DENSE, s);
+  if (a.m > CE_MAXM || a.m < 1 || a.k < 0 || a.k >= a.m) return cudaErrorInvalidValue;
+  const size_t smem = gmresdr_cycle_end_smem(a.m);
+  cudaError_t e = cudaFuncSetAttribute(gmresdr_cycle_end_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)gmresdr_cycle_end_smem(CE_MAXM));
+  if (e != cudaSuccess) return e;
+  gmresdr_cycle_end_kernel<<<1, CE_THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace wd

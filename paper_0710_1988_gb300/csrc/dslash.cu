@@ -1,0 +1,240 @@
+// Wilson-Dirac operator A = 1 - kappa*D + i*mu*gamma5 in FP64 (Sec. 1, Sec. 4).
+//
+// One thread per (site, right-hand side).  Each of the 8 hops projects the
+// neighbour spinor onto the 2-spin subspace of (1 -/+ gamma_mu), multiplies
+// the two colour vectors by the link (or its adjoint) and rebuilds the
+// lower spin pair from the upper one, so a hop costs 2 SU(3) mat-vecs
+// instead of 4.  In the chiral basis gamma_mu = [[0, B], [B^dagger, 0]]
+// with B = -i sigma_k (k = x, y, z) and B = 1 (t):
+//   (1 - gamma_mu) psi = [h ; -B^dagger h],  h = psi_up - B psi_dn
+//   (1 + gamma_mu) psi = [h ; +B^dagger h],  h = psi_up + B psi_dn
+// A^dagger = gamma5 A(-mu) gamma5 (gamma5-hermiticity, Sec. 1) swaps the
+// two projectors and flips the sign of mu.
+//
+// Optional fused epilogues write one block-partial (3 doubles) per block for
+// the BiCGStab scalars: EPI_DOT   <aux, out>, <out, out>   (aux = r_hat)
+//                       EPI_TSTT  <out, in>,  <out, out>
+#include "cplx.cuh"
+#include "wd_internal.h"
+#include "kernels.cuh"
+
+namespace wd {
+
+// spinor component c = 3*sigma + a
+template <int MU, int S>  // S = -1: (1 - gamma_mu), S = +1: (1 + gamma_mu)
+__device__ __forceinline__ void project(const double2 (&p)[12], double2 (&h)[6]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double2 p0 = p[a], p1 = p[3 + a], p2 = p[6 + a], p3 = p[9 + a];
+    if (MU == 0) {        // B psi_dn = (-i p3, -i p2)
+      h[a] = S < 0 ? cadd(p0, cmuli(p3)) : csub(p0, cmuli(p3));
+      h[3 + a] = S < 0 ? cadd(p1, cmuli(p2)) : csub(p1, cmuli(p2));
+    } else if (MU == 1) { // B psi_dn = (-p3, p2)
+      h[a] = S < 0 ? cadd(p0, p3) : csub(p0, p3);
+      h[3 + a] = S < 0 ? csub(p1, p2) : cadd(p1, p2);
+    } else if (MU == 2) { // B psi_dn = (-i p2, i p3)
+      h[a] = S < 0 ? cadd(p0, cmuli(p2)) : csub(p0, cmuli(p2));
+      h[3 + a] = S < 0 ? csub(p1, cmuli(p3)) : cadd(p1, cmuli(p3));
+    } else {              // B psi_dn = (p2, p3)
+      h[a] = S < 0 ? csub(p0, p2) : cadd(p0, p2);
+      h[3 + a] = S < 0 ? csub(p1, p3) : cadd(p1, p3);
+    }
+  }
+}
+
+// acc += [chi ; S * B^dagger chi]
+template <int MU, int S>
+__device__ __forceinline__ void reconstruct(double2 (&acc)[12], const double2 (&c)[6]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double2 c0 = c[a], c1 = c[3 + a];
+    acc[a] = cadd(acc[a], c0);
+    acc[3 + a] = cadd(acc[3 + a], c1);
+    if (MU == 0) {        // B^dagger chi = (i c1, i c0)
+      acc[6 + a] = S < 0 ? csub(acc[6 + a], cmuli(c1)) : cadd(acc[6 + a], cmuli(c1));
+      acc[9 + a] = S < 0 ? csub(acc[9 + a], cmuli(c0)) : cadd(acc[9 + a], cmuli(c0));
+    } else if (MU == 1) { // B^dagger chi = (c1, -c0)
+      acc[6 + a] = S < 0 ? csub(acc[6 + a], c1) : cadd(acc[6 + a], c1);
+      acc[9 + a] = S < 0 ? cadd(acc[9 + a], c0) : csub(acc[9 + a], c0);
+    } else if (MU == 2) { // B^dagger chi = (i c0, -i c1)
+      acc[6 + a] = S < 0 ? csub(acc[6 + a], cmuli(c0)) : cadd(acc[6 + a], cmuli(c0));
+      acc[9 + a] = S < 0 ? cadd(acc[9 + a], cmuli(c1)) : csub(acc[9 + a], cmuli(c1));
+    } else {              // B^dagger chi = (c0, c1)
+      acc[6 + a] = S < 0 ? csub(acc[6 + a], c0) : cadd(acc[6 + a], c0);
+      acc[9 + a] = S < 0 ? csub(acc[9 + a], c1) : cadd(acc[9 + a], c1);
+    }
+  }
+}
+
+// chi = U h (ADJ = false) or U^dagger h (ADJ = true), two colour vectors
+template <bool ADJ>
+__device__ __forceinline__ void su3_mul(const double2 *__restrict__ u, const double2 (&h)[6],
+                                        double2 (&c)[6]) {
+  double2 m[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) m[i] = __ldg(u + i);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) {
+      double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        if (ADJ)
+          acc = cfmac(m[3 * b + a], h[3 * sp + b], acc);
+        else
+          acc = cfma(m[3 * a + b], h[3 * sp + b], acc);
+      }
+      c[3 * sp + a] = acc;
+    }
+  }
+}
+
+__device__ __forceinline__ void load_spinor(const double2 *__restrict__ p, double2 (&v)[12]) {
+#pragma unroll
+  for (int i = 0; i < 12; ++i) v[i] = __ldg(p + i);
+}
+
+template <int MU, int S, bool ADJ>
+__device__ __forceinline__ void hop(const double2 *__restrict__ psi,
+                                    const double2 *__restrict__ links, long long q,
+                                    long long ql, double2 (&acc)[12]) {
+  double2 p[12], h[6], c[6];
+  load_spinor(psi + 12 * q, p);
+  project<MU, S>(p, h);
+  su3_mul<ADJ>(links + (ql * 4 + MU) * 9, h, c);
+  reconstruct<MU, S>(acc, c);
+}
+
+template <bool DAG, int EPI>
+__global__ void __launch_bounds__(128)
+wilson_f64_kernel(const double2 *__restrict__ links, const double2 *__restrict__ in,
+                  double2 *__restrict__ out, LatticeGeom g, double kappa, double mu,
+                  const double2 *__restrict__ aux, double *__restrict__ partial,
+                  const int *__restrict__ status, unsigned mask,
+                  unsigned long long *__restrict__ sites) {
+  const int r = blockIdx.y;
+  if (status != nullptr && !((mask >> status[r]) & 1u)) return;  // uniform per block
+  if (sites != nullptr && blockIdx.x == 0 && threadIdx.x == 0)
+    atomicAdd(sites, (unsigned long long)g.V);  // work accounting for the profiler
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const double2 *psi = in + (long long)r * 12 * g.V;
+  double red[3] = {0.0, 0.0, 0.0};
+  if (s < g.V) {
+    const int x = (int)(s % g.L[0]);
+    long long t1 = s / g.L[0];
+    const int y = (int)(t1 % g.L[1]);
+    t1 /= g.L[1];
+    const int z = (int)(t1 % g.L[2]);
+    const int t = (int)(t1 / g.L[2]);
+    const long long sx = 1, sy = g.L[0], sz = sy * g.L[1], st = sz * g.L[2];
+    const long long xp = x + 1 == g.L[0] ? s - (g.L[0] - 1) * sx : s + sx;
+    const long long xm = x == 0 ? s + (g.L[0] - 1) * sx : s - sx;
+    const long long yp = y + 1 == g.L[1] ? s - (g.L[1] - 1) * sy : s + sy;
+    const long long ym = y == 0 ? s + (g.L[1] - 1) * sy : s - sy;
+    const long long zp = z + 1 == g.L[2] ? s - (g.L[2] - 1) * sz : s + sz;
+    const long long zm = z == 0 ? s + (g.L[2] - 1) * sz : s - sz;
+    const long long tp = t + 1 == g.L[3] ? s - (g.L[3] - 1) * st : s + st;
+    const long long tm = t == 0 ? s + (g.L[3] - 1) * st : s - st;
+
+    constexpr int F = DAG ? +1 : -1;  // projector sign on forward hops
+    constexpr int B = -F;             // and on backward hops
+    double2 acc[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) acc[i] = make_double2(0.0, 0.0);
+    hop<0, F, false>(psi, links, xp, s, acc);
+    hop<0, B, true>(psi, links, xm, xm, acc);
+    hop<1, F, false>(psi, links, yp, s, acc);
+    hop<1, B, true>(psi, links, ym, ym, acc);
+    hop<2, F, false>(psi, links, zp, s, acc);
+    hop<2, B, true>(psi, links, zm, zm, acc);
+    hop<3, F, false>(psi, links, tp, s, acc);
+    hop<3, B, true>(psi, links, tm, tm, acc);
+
+    double2 p[12];
+    load_spinor(psi + 12 * s, p);
+    const double tmu = DAG ? -mu : mu;
+    double2 *o = out + (long long)r * 12 * g.V + 12 * s;
+    const double2 *ax = (EPI == EPI_DOT) ? aux + (long long)r * 12 * g.V + 12 * s : nullptr;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      double2 v;
+      v.x = fma(-kappa, acc[c].x, p[c].x);
+      v.y = fma(-kappa, acc[c].y, p[c].y);
+      if (tmu != 0.0) {  // + i mu gamma5 psi, gamma5 = diag(1, 1, -1, -1)
+        const double m = c < 6 ? tmu : -tmu;
+        v.x = fma(-m, p[c].y, v.x);
+        v.y = fma(m, p[c].x, v.y);
+      }
+      o[c] = v;
+      if (EPI == EPI_DOT) {  // <aux, out> = sum conj(aux) out
+        const double2 a = __ldg(ax + c);
+        red[0] = fma(a.x, v.x, red[0]);
+        red[0] = fma(a.y, v.y, red[0]);
+        red[1] = fma(a.x, v.y, red[1]);
+        red[1] = fma(-a.y, v.x, red[1]);
+        red[2] = fma(v.x, v.x, red[2]);
+        red[2] = fma(v.y, v.y, red[2]);
+      } else if (EPI == EPI_TSTT) {  // <out, in> and <out, out>
+        red[0] = fma(v.x, p[c].x, red[0]);
+        red[0] = fma(v.y, p[c].y, red[0]);
+        red[1] = fma(v.x, p[c].y, red[1]);
+        red[1] = fma(-v.y, p[c].x, red[1]);
+        red[2] = fma(v.x, v.x, red[2]);
+        red[2] = fma(v.y, v.y, red[2]);
+      }
+    }
+  }
+  if (EPI != EPI_NONE) {
+    constexpr int NQ = 3;
+    block_sum<NQ>(red);
+    if (threadIdx.x == 0) {
+      double *dst = partial + ((long long)r * gridDim.x + blockIdx.x) * NQ;
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) dst[q] = red[q];
+    }
+  }
+}
+
+LatticeGeom geom_of(const wd_context *h) {
+  LatticeGeom g;
+  for (int i = 0; i < 4; ++i) g.L[i] = h->dims[i];
+  g.V = h->V;
+  return g;
+}
+
+int wilson_blocks(const wd_context *h) { return (int)((h->V + 127) / 128); }
+
+cudaError_t launch_wilson_f64_epi(const wd_context *h, const double2 *in, double2 *out,
+                                  int nrhs, int dagger, int epi, const double2 *aux,
+                                  double *partial, const int *status, cudaStream_t s,
+                                  unsigned mask) {
+  dim3 grid(wilson_blocks(h), nrhs);
+  LatticeGeom g = geom_of(h);
+  ProfLaunch prof(PC_DSLASH, s);
+  unsigned long long *cnt = prof_site_counter();
+  if (dagger) {
+    if (epi == EPI_DOT)
+      wilson_f64_kernel<true, EPI_DOT><<<grid, 128, 0, s>>>(h->links, in, out, g, h->kappa, h->mu, aux, partial, status, mask, cnt);
+    else if (epi == EPI_TSTT)
+      wilson_f64_kernel<true, EPI_TSTT><<<grid, 128, 0, s>>>(h->links, in, out, g, h->kappa, h->mu, aux, partial, status, mask, cnt);
+    else
+      wilson_f64_kernel<true, EPI_NONE><<<grid, 128, 0, s>>>(h->links, in, out, g, h->kappa, h->mu, aux, partial, status, mask, cnt);
+  } else {
+    if (epi == EPI_DOT)
+      wilson_f64_kernel<false, EPI_DOT><<<grid, 128, 0, s>>>(h->links, in, out, g, h->kappa, h->mu, aux, partial, status, mask, cnt);
+    else if (epi == EPI_TSTT)
+      wilson_f64_kernel<false, EPI_TSTT><<<grid, 128, 0, s>>>(h->links, in, out, g, h->kappa, h->mu, aux, partial, status, mask, cnt);
+    else
+      wilson_f64_kernel<false, EPI_NONE><<<grid, 128, 0, s>>>(h->links, in, out, g, h->kappa, h->mu, aux, partial, status, mask, cnt);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wilson_f64(const wd_context *h, const double2 *in, double2 *out, int nrhs,
+                              int dagger, cudaStream_t s) {
+  return launch_wilson_f64_epi(h, in, out, nrhs, dagger, EPI_NONE, nullptr, nullptr, nullptr, s,
+                               M_ALL);
+}
+
+}  // namespace wd

@@ -1,0 +1,148 @@
+// Kernel-level declarations shared by the CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "wd_internal.h"
+
+namespace wd {
+
+struct LatticeGeom {
+  int L[4];
+  long long V;
+};
+
+enum { EPI_NONE = 0, EPI_DOT = 1, EPI_TSTT = 2 };
+
+// Per-system solver status.  Kernels take a bit mask of the statuses they
+// act on and skip every other system.
+enum SysStatus {
+  ST_ACTIVE = 0,       // iterating
+  ST_RECURSIVE = 1,    // recursive residual below tol: check the true one
+  ST_BREAKDOWN = 2,    // final
+  ST_MAXITER = 3,      // final
+  ST_DONE = 4,         // true residual below tol: final
+  ST_FAILED = 5,       // true residual above tol, restarts used up: final
+  ST_RESTART = 6,      // transient: restart from the true residual
+  ST_IDLE = 7          // not part of this phase
+};
+constexpr unsigned M_ACTIVE = 1u << ST_ACTIVE;
+constexpr unsigned M_RECURSIVE = 1u << ST_RECURSIVE;
+constexpr unsigned M_RESTART = 1u << ST_RESTART;
+constexpr unsigned M_ALL = 0xffffffffu;
+
+// BiCGStab scalars of one system, device resident.
+struct BicgScalars {
+  double2 rho, rho_old, alpha, omega;
+  double bnorm, rhat_norm, rnorm, true_rel, tol;
+  int iters, max_iter, restarts, max_restarts;
+  long long mvp, mvp_extra;
+};
+
+LatticeGeom geom_of(const wd_context *h);
+int wilson_blocks(const wd_context *h);
+
+// Wilson apply with an optional fused reduction epilogue; blocks of systems
+// whose status is not in `mask` do nothing (status == nullptr: all act).
+cudaError_t launch_wilson_f64_epi(const wd_context *h, const double2 *in, double2 *out,
+                                  int nrhs, int dagger, int epi, const double2 *aux,
+                                  double *partial, const int *status, cudaStream_t s,
+                                  unsigned mask = M_ACTIVE);
+
+// ----------------------------------------------------------------- BLAS1
+// Number of blocks (per system) every streaming kernel uses; fixed so that
+// the reduction order, and hence every result, is reproducible.
+int stream_blocks(long long n);
+
+cudaError_t launch_bicg_update_p(double2 *p, const double2 *r, const double2 *v,
+                                 const BicgScalars *sc, const int *status, long long n,
+                                 int nrhs, cudaStream_t s);
+cudaError_t launch_bicg_update_s(double2 *sv, const double2 *r, const double2 *v,
+                                 const BicgScalars *sc, const int *status, long long n,
+                                 int nrhs, cudaStream_t s);
+cudaError_t launch_bicg_update_xr(double2 *x, double2 *r, const double2 *p, const double2 *sv,
+                                  const double2 *t, const double2 *rhat, const BicgScalars *sc,
+                                  const int *status, double *partial, long long n, int nrhs,
+                                  cudaStream_t s);
+// out = a - b, partial <- ||out||^2 ; systems in mask only
+cudaError_t launch_sub_norm(double2 *out, const double2 *a, const double2 *b, const int *status,
+                            unsigned mask, double *partial, long long n, int nrhs,
+                            cudaStream_t s);
+// partial <- ||a||^2 (and ||b||^2 when b != nullptr), all systems
+cudaError_t launch_norms(const double2 *a, const double2 *b, double *partial, long long n,
+                         int nrhs, cudaStream_t s);
+// for systems in mask: rhat = r, p = 0, v = 0
+cudaError_t launch_bicg_restart_vectors(double2 *rhat, const double2 *r, double2 *p,
+                                        double2 *v, const int *status, unsigned mask,
+                                        long long n, int nrhs, cudaStream_t s);
+
+// Scalar finalizers (one block per system): reduce nb block partials of NQ
+// doubles in a fixed order, then update the scalars and status.
+enum FinKind { FIN_INIT, FIN_ALPHA, FIN_OMEGA, FIN_RHO, FIN_TRUE, FIN_ACTIVATE };
+cudaError_t launch_bicg_finalize(int kind, const double *partial, int nb, BicgScalars *sc,
+                                 int *status, double *hist, int hist_len, int nrhs,
+                                 cudaStream_t s);
+
+// ----------------------------------------------------------------- tall-skinny
+// C[j][r] = sum_i conj(V[j][i]) * (g5 ? gamma5 W[r] : W[r])[i],  j < k, r < nrhs.
+// Block partials (ts_dot_blocks of them, k*nrhs each) go to `partial`;
+// launch_ts_dot_finalize sums them in block order into C[j*ldc + r] and,
+// when C2 != nullptr, also adds them to C2[j*ldc2 + r].  k + nrhs <= 176.
+constexpr int TS_MAX_ROWS = 176;  // k + nrhs
+constexpr int TS_MAX_BLOCKS = 304;  // upper bound of ts_dot_blocks()
+int ts_dot_blocks(long long n, int k, int nrhs);
+cudaError_t launch_ts_dot(const double2 *V, int k, const double2 *W, int nrhs, int g5,
+                          long long n, double2 *partial, const int *status,
+                          cudaStream_t s);
+cudaError_t launch_ts_dot_finalize(const double2 *partial, int nb, int k, int nrhs,
+                                   double2 *C, int ldc, double2 *C2, int ldc2,
+                                   const int *status, cudaStream_t s);
+// OUT[c][i] = (beta_one ? IN[c][i] : 0) + sign * sum_j V[j][i] Y[j*ldy + c],
+// c < ncol, kv <= 128.  OUT may alias IN (in-place update) but not V.
+cudaError_t launch_ts_update(const double2 *V, int kv, const double2 *Y, int ldy, int ncol,
+                             const double2 *IN, double2 *OUT, int beta_one, double sign,
+                             long long n, const int *status, cudaStream_t s);
+
+// ----------------------------------------------------------------- Arnoldi helpers
+// partial -> ||w||^2 reduced; H[(j+1)*ldh + j] = ||w||; v = w / ||w||;
+// lucky breakdown when ||w|| <= lucky * ||w0|| sets *status = 1 and m_eff.
+cudaError_t launch_arnoldi_normalize_finalize(const double *partial_w, int nb,
+                                              const double *partial_w0, int nb0,
+                                              double2 *H, int ldh, int j, double lucky,
+                                              int *status, int *m_eff, cudaStream_t s);
+// *dst = sqrt(sum_i partial[i*stride]) for i < nb (deterministic order)
+cudaError_t launch_norm_finalize(const double *partial, int nb, int stride, double2 *dst,
+                                 cudaStream_t s);
+// v = w / Re(H[idx]) unless *status != 0
+cudaError_t launch_scale_by_inverse_entry(double2 *v, const double2 *w, const double2 *H,
+                                          int idx, long long n, const int *status,
+                                          cudaStream_t s);
+
+// ----------------------------------------------------------------- small dense (1 CTA)
+// LU with partial pivoting of a k x k matrix (row-major), in place; piv[k].
+// info[0] = 0 ok, 1 singular; info[1] bits of an estimate of cond (double).
+cudaError_t launch_lu_factor(double2 *A, int k, int *piv, double *info, cudaStream_t s);
+// Solve A Y = C for nrhs columns (C row-major k x nrhs, overwritten by Y).
+cudaError_t launch_lu_solve(const double2 *LU, const int *piv, int k, double2 *C, int nrhs,
+                            cudaStream_t s);
+
+struct CycleEndArgs {
+  const double2 *H;    // (m+1) x m row-major Hbar_m
+  const double2 *c;    // m+1
+  int m, k;
+  const int *m_eff;    // Arnoldi columns actually built (lucky breakdown)
+  double2 *d;          // m: least-squares solution
+  double2 *rho;        // m+1: c - Hbar d
+  double *res;         // [0] ||rho||
+  double2 *P;          // (m+1) x (k+1) row-major
+  double2 *Hk;         // (k+1) x k row-major: P^dagger Hbar P_k
+  double2 *ck;         // k+1: P^dagger rho
+  double2 *theta;      // k harmonic Ritz values
+  int *flags;          // [0] eig failure, [1] lucky
+  double2 *work;       // scratch >= 4*(m+1)*(m+1) complex
+  int do_restart;
+};
+cudaError_t launch_gmresdr_cycle_end(const CycleEndArgs &a, cudaStream_t s);
+size_t gmresdr_cycle_end_smem(int m);
+
+}  // namespace wd

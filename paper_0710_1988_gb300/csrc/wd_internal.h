@@ -1,0 +1,101 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/wd.h"
+#include "profile.h"
+
+namespace wd {
+
+// ----------------------------------------------------------------- errors
+
+void set_error(const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define WD_CK(call)                                                      \
+  do {                                                                   \
+    cudaError_t e_ = (call);                                             \
+    if (e_ != cudaSuccess) return ::wd::cuda_fail(e_, #call);           \
+  } while (0)
+
+#define WD_CK_LAUNCH(what)                                               \
+  do {                                                                   \
+    cudaError_t e_ = cudaGetLastError();                                 \
+    if (e_ != cudaSuccess) return ::wd::cuda_fail(e_, what);            \
+  } while (0)
+
+// ----------------------------------------------------------------- memory
+
+// Stream-ordered device scratch: every take() is a cudaMallocFromPoolAsync on
+// the handle's own memory pool (release threshold = unlimited, so freed
+// blocks stay cached for the next call), and release() frees them all on
+// the same stream.  A failed take() returns nullptr and sets `failed`.
+struct Arena {
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t stream = nullptr;
+  std::vector<void *> ptrs;
+  bool failed = false;
+  template <class T> T *take(size_t count) {
+    void *p = nullptr;
+    size_t bytes = count * sizeof(T);
+    if (bytes < 256) bytes = 256;
+    if (failed || cudaMallocFromPoolAsync(&p, bytes, pool, stream) != cudaSuccess) {
+      failed = true;
+      return nullptr;
+    }
+    ptrs.push_back(p);
+    return reinterpret_cast<T *>(p);
+  }
+  void release() {
+    for (void *p : ptrs) cudaFreeAsync(p, stream);
+    ptrs.clear();
+  }
+};
+
+inline size_t aligned_bytes(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Pointer classification for "device or host" arguments.
+bool is_device_pointer(const void *p);
+
+}  // namespace wd
+
+// The handle.
+struct wd_context {
+  int dims[4];
+  long long V;      // sites
+  long long n;      // 12 V complex numbers per spinor
+  double kappa;
+  double mu;
+  int device;
+  double2 *links;   // device, [V][4][3][3] complex128
+  cudaMemPool_t pool;  // this handle's scratch pool
+  wd::Profiler prof;   // optional kernel timing
+};
+
+struct wd_deflation_space {
+  wd_context *h;
+  int k;
+  double2 *V;       // [k][n]
+  double2 *U;       // [k][n], nullptr means gamma5 V
+  double2 *W;       // [k][n] = A V
+  double2 *LU;      // [k][k] row-major LU factors of G = U^dagger A V
+  int *piv;         // [k]
+  double kappa, mu; // operator parameters W and G were built for
+};
+
+namespace wd {
+
+// ----------------------------------------------------------------- kernels
+// Every launcher enqueues on `s` and returns cudaGetLastError().
+
+// out[r] = A in[r] (dagger: A^dagger), r < nrhs; n-vectors in boundary layout.
+cudaError_t launch_wilson_f64(const wd_context *h, const double2 *in,
+                              double2 *out, int nrhs, int dagger,
+                              cudaStream_t s);
+
+}  // namespace wd

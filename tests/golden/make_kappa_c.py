@@ -31,7 +31,9 @@ def main(names):
         kc = kappa.kappa_c(U, cfg.dims)
         table[name] = {"dims": list(cfg.dims), "eps": cfg.eps,
                        "link_seed": L.link_seed(cfg), "kappa_c": kc,
-                       "method": "dense eig" if 12 * U.shape[0] <= 3072 else "Arnoldi (eigs LR)"}
+                       "method": ("dense eig" if 12 * U.shape[0] <= 3072 else
+                                  "Arnoldi (eigs LR, tol 1e-10)" if 12 * U.shape[0] <= 100_000
+                                  else "Arnoldi (eigs LR, tol 1e-6)")}
         print(f"{name}: kappa_c = {kc!r}  ({time.time() - t0:.0f} s)", flush=True)
         with open(OUT, "w") as f:
             json.dump(table, f, indent=1, sort_keys=True)
