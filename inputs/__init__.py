@@ -23,10 +23,11 @@ from .lattice import (
     link_seed,
     rhs_seed,
     source,
+    move_links,
 )
 
 __all__ = [
     "LatticeConfig", "CONFIGS", "volume", "gauge_field", "unit_gauge_field",
     "gaussian_spinor", "z4_spinor", "random_su3", "gauge_transform_field",
-    "link_seed", "rhs_seed", "source",
+    "link_seed", "rhs_seed", "source", "move_links",
 ]

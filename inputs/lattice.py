@@ -137,6 +137,16 @@ def gauge_transform_field(dims, seed: int, eps: float = 1.5) -> np.ndarray:
     return np.ascontiguousarray(random_su3(rng, (volume(dims),), eps))
 
 
+def move_links(links: np.ndarray, omega: np.ndarray, h: float) -> np.ndarray:
+    """Links displaced along Lie-algebra directions: exp(i h omega_a lambda_a/2) U.
+
+    omega has shape (V, 4, 8); used to build finite-difference inputs."""
+    herm = np.einsum("sma,aij->smij", omega, GELL_MANN) * (0.5 * h)
+    w, q = np.linalg.eigh(herm)
+    ex = np.einsum("...ij,...j,...kj->...ik", q, np.exp(1j * w), np.conj(q))
+    return np.ascontiguousarray(ex @ links)
+
+
 # ---------------------------------------------------------------- sources
 
 def gaussian_spinor(dims, seed: int, nrhs: Optional[int] = None) -> np.ndarray:

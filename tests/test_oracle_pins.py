@@ -203,6 +203,54 @@ def test_apply_at_sites_matches_field_apply():
     assert np.abs(full[sites] - part).max() < 1e-14
 
 
+# ------------------------------------------------------------------ even-odd
+
+def test_eo_compact_index():
+    from oracle import evenodd
+    for dims in [(4, 2, 2, 4), (6, 4, 2, 2)]:
+        v = L.volume(dims)
+        for p in (0, 1):
+            assert np.array_equal(evenodd.sites(dims, p) // 2, np.arange(v // 2))
+
+
+def _dense_schur(U, dims, kap, mu):
+    from oracle import evenodd
+    nh = 12 * L.volume(dims) // 2
+    M = np.zeros((nh, nh), dtype=complex)
+    e = np.zeros(nh, dtype=complex)
+    for j in range(nh):
+        e[:] = 0
+        e[j] = 1
+        M[:, j] = evenodd.schur_apply(U, dims, kap, mu, e).ravel()
+    return M
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.1])
+def test_eo_schur_solve_equals_full_solve(mu):
+    from oracle import evenodd
+    dims = (4, 2, 2, 4)
+    U = L.gauge_field(dims, 0.5, 4300)
+    kap = 0.12
+    b = L.gaussian_spinor(dims, 4301)
+    A = dirac.dense_A(U, dims, kap, mu)
+    x_full = np.linalg.solve(A, b.ravel())
+    Ah = _dense_schur(U, dims, kap, mu)
+    xe = np.linalg.solve(Ah, evenodd.prepare(U, dims, kap, mu, b).ravel())
+    x = evenodd.reconstruct(U, dims, kap, mu, b, xe)
+    assert np.abs(x.ravel() - x_full).max() <= 1e-12 * np.abs(x_full).max()
+
+
+def test_eo_schur_gamma5_hermiticity():
+    dims = (4, 2, 2, 4)
+    U = L.gauge_field(dims, 0.5, 4302)
+    nh = 12 * L.volume(dims) // 2
+    g5 = np.kron(np.eye(nh // 12), np.kron(dirac.GAMMA5, np.eye(3)))
+    for mu in (0.0, 0.07):
+        Ap = _dense_schur(U, dims, 0.13, mu)
+        Am = _dense_schur(U, dims, 0.13, -mu)
+        assert np.abs(g5 @ Ap @ g5 - Am.conj().T).max() < 1e-14
+
+
 # ------------------------------------------------------------------ twisted mass
 
 def test_twisted_mass_identities():
@@ -229,6 +277,13 @@ def test_kappa_c_free_field():
     assert abs(kappa.kappa_c_dense(L.unit_gauge_field(dims), dims) - 0.125) < 1e-14
     dims = (4, 4, 4, 4)
     assert abs(kappa.kappa_c_arnoldi(L.unit_gauge_field(dims), dims) - 0.125) < 1e-10
+
+
+def test_kappa_c_krylov_full_space_is_exact():
+    # with as many steps as the dimension the Ritz values are the eigenvalues
+    dims = (2, 2, 2, 2)
+    U = L.gauge_field(dims, 0.3, 72)
+    assert abs(kappa.kappa_c_krylov(U, dims, steps=192) - kappa.kappa_c_dense(U, dims)) < 1e-10
 
 
 def test_kappa_c_three_ways_agree():
