@@ -88,6 +88,25 @@ typedef struct {
 int wd_create(const int lat[4], const void *links, double kappa, double mu,
               wd_handle *out);
 
+/* Select the operator every vector entry point acts on: even_odd = 0 is A
+ * on full vectors (n = 12 V); even_odd = 1 is the even-odd Schur complement
+ * of Sec. 3 ("the even-odd preconditioned system"),
+ *   A_hat = (1 + i mu gamma5) - kappa^2 D_eo (1 + i mu gamma5)^{-1} D_oe,
+ * on even-site half vectors (n = 6 V complex128, site s of parity 0 stored at
+ * s / 2).  Needs all extents even.  wd_apply, gmresdr_solve, the deflation
+ * and D-BiCGStab entry points and tm_multishift_solve then use A_hat and
+ * half vectors; the FP32 path and wd_gradients need even_odd = 0. */
+int wd_set_operator(wd_handle h, int even_odd);
+
+/* Even-odd helpers (handle in even-odd mode; device pointers; nrhs vectors):
+ *  wd_eo_prepare:     Bhat = b_e + kappa D_eo (1 + i mu gamma5)^{-1} b_o
+ *                     (B full, Bhat half).
+ *  wd_eo_reconstruct: X = [x_e ; x_o], x_o = (1 + i mu gamma5)^{-1}
+ *                     (b_o + kappa D_oe x_e) (B, X full, Xe half). */
+int wd_eo_prepare(wd_handle h, const void *B, void *Bhat, int nrhs, wd_stream stream);
+int wd_eo_reconstruct(wd_handle h, const void *B, const void *Xe, void *X, int nrhs,
+                      wd_stream stream);
+
 /* Change kappa and mu of an existing handle (no data movement). */
 int wd_set_params(wd_handle h, double kappa, double mu);
 
@@ -146,6 +165,64 @@ int dbicgstab_solve_deflated(wd_handle h, wd_deflation d, const void *B,
 int dbicgstab_solve(wd_handle h, const void *B, void *X, int nrhs,
                     const void *V, const void *U, int k, double tol,
                     int max_iter, wd_stats *stats, wd_stream stream);
+
+/* ---------------------------------------------------------- Sec. 4 shifts */
+
+/* Twisted-mass systems A(mu_i) x_i = b for shifts mu_0, mu_1, ... solved
+ * serially in the given order (Sec. 4; the paper prefers heaviest first).
+ * With project != 0, before shift i every right-hand side is projected over
+ * its own earlier solutions Q = [x_0 .. x_{i-1}]: Q^dagger A_i^dagger A_i Q d
+ * = Q^dagger A_i^dagger b, x0 = Q d (i products per right-hand side, counted
+ * in mvp_extra); then BiCGStab (FP64, or mixed = 1 for the FP32 iteration
+ * with FP64 reliable updates) from x0 for all right-hand sides at once.
+ * The handle's kappa is used for every shift; its mu is restored on return.
+ *  B: device, nrhs*n complex128.  X: device, nshift*nrhs*n complex128,
+ *  X[i][r] = solution of shift i, right-hand side r.  mus: host, nshift.
+ *  stats: NULL or host array of nshift*nrhs, [i][r]. */
+int tm_multishift_solve(wd_handle h, const void *B, void *X, int nrhs,
+                        const double *mus, int nshift, double tol, int max_iter,
+                        int project, int mixed, wd_stats *stats, wd_stream stream);
+
+/* ---------------------------------------------------------- differentiation */
+
+/* Not in the paper: gradients of a real loss through x = A^{-1} b.
+ * LAM = A^{-dagger} G for nrhs right-hand sides, by gamma5-hermiticity
+ * (Sec. 1): A^dagger = gamma5 A(-mu) gamma5, so LAM = gamma5 A(-mu)^{-1}
+ * gamma5 G is one more D-BiCGStab solve with the same operator when mu = 0
+ * (then the deflation space of A serves; for mu != 0 pass d = NULL or a
+ * space built for -mu).  G, LAM: device, nrhs*n complex128. */
+int dbicgstab_solve_adjoint(wd_handle h, wd_deflation d, const void *G, void *LAM,
+                            int nrhs, double tol, int max_iter, wd_stats *stats,
+                            wd_stream stream);
+
+/* For L real with dL = Re(g^dagger dx), x = A^{-1} b and lam = A^{-dagger} g:
+ *  force  (NULL or device, V*4*8 double, [site][mu][a]): dL/domega for links
+ *         moved as U_mu(s) -> exp(i omega_a lambda_a/2) U_mu(s) (Gell-Mann
+ *         lambda_a), i.e. -kappa Im tr[lambda_a/2 (W1 - W2)], see force.cu;
+ *  dkappa (NULL or host double): dL/dkappa = Re(lam^dagger D x).
+ * (dL/db = lam itself.)  lam, x: device, n complex128 (one right-hand side). */
+int wd_gradients(wd_handle h, const void *lam, const void *x, void *force,
+                 double *dkappa, wd_stream stream);
+
+/* ---------------------------------------------------------- mixed precision */
+
+/* The same D-BiCGStab(k) solve with the BiCGStab iteration in FP32 storage
+ * and arithmetic (vectors, links and Wilson apply) and FP64 reliable
+ * updates: every `reliable_every` iterations, and when the FP32 recursive
+ * residual reaches tol, x is accumulated in FP64 and r = b - A x is
+ * recomputed with the FP64 operator.  The deflation projection (Sec. 2)
+ * and the convergence test (FP64 true residual <= tol) are FP64.  Arguments
+ * and results as dbicgstab_solve_deflated; reliable_every >= 1 (50 is the
+ * workload's choice).  Not in the paper, which states no precision. */
+int dbicgstab_solve_mixed(wd_handle h, wd_deflation d, const void *B, void *X,
+                          int nrhs, double tol, int max_iter, int reliable_every,
+                          wd_stats *stats, wd_stream stream);
+
+/* out = A in (dagger = 0) or A^dagger in, computed by the FP32 kernel of
+ * the mixed solver: in and out are FP64 device vectors in the boundary
+ * layout, rounded to FP32 on entry and widened on exit. */
+int wd_apply_f32(wd_handle h, const void *in, void *out, int nrhs, int dagger,
+                 wd_stream stream);
 
 /* ---------------------------------------------------------- instrumentation */
 

@@ -94,11 +94,32 @@ class WilsonOperator:
         self.kappa, self.mu = float(kappa), float(mu)
         check(lib().wd_set_params(self._h, self.kappa, self.mu))
 
+    def set_operator(self, even_odd: bool):
+        """Full operator (False) or the even-odd Schur complement on even-site
+        half vectors (True); see wd_set_operator."""
+        check(lib().wd_set_operator(self._h, 1 if even_odd else 0))
+        self.even_odd = bool(even_odd)
+
+    def eo_prepare(self, B, Bhat, stream=None):
+        nrhs = _numel(B) // (12 * self.volume)
+        check(lib().wd_eo_prepare(self._h, _ptr(B), _ptr(Bhat), nrhs, _stream(stream, B, Bhat)))
+        return Bhat
+
+    def eo_reconstruct(self, B, Xe, X, stream=None):
+        nrhs = _numel(B) // (12 * self.volume)
+        check(lib().wd_eo_reconstruct(self._h, _ptr(B), _ptr(Xe), _ptr(X), nrhs,
+                                      _stream(stream, B, Xe, X)))
+        return X
+
+    @property
+    def op_n(self) -> int:
+        return self.n // 2 if getattr(self, "even_odd", False) else self.n
+
     def _nrhs(self, a) -> int:
         n = _numel(a)
-        if n % self.n:
-            raise ValueError("vector length is not a multiple of 12*V")
-        return n // self.n
+        if n % self.op_n:
+            raise ValueError("vector length is not a multiple of the operator's vector length")
+        return n // self.op_n
 
     # -- operator
     def apply(self, x, out, dagger: bool = False, stream=None):
@@ -142,6 +163,66 @@ class WilsonOperator:
             nrhs, float(tol), int(max_iter), sts, _stream(stream, B, X))
         check(rc, allow=(_lib.WD_OK, _lib.WD_NOT_CONVERGED, _lib.WD_BREAKDOWN))
         return rc, [s.as_dict() for s in sts]
+
+    def dbicgstab_mixed(self, B, X, deflation: Optional["Deflation"] = None,
+                        tol: float = 1e-10, max_iter: int = 100000, reliable_every: int = 50,
+                        stream=None):
+        """As dbicgstab, with the iteration in FP32 and FP64 reliable updates."""
+        nrhs = self._nrhs(B)
+        sts = (WdStats * nrhs)()
+        rc = lib().dbicgstab_solve_mixed(
+            self._h, deflation._d if deflation is not None else None, _ptr(B), _ptr(X),
+            nrhs, float(tol), int(max_iter), int(reliable_every), sts, _stream(stream, B, X))
+        check(rc, allow=(_lib.WD_OK, _lib.WD_NOT_CONVERGED, _lib.WD_BREAKDOWN))
+        return rc, [s.as_dict() for s in sts]
+
+    def adjoint_solve(self, G, LAM, deflation: Optional["Deflation"] = None,
+                      tol: float = 1e-10, max_iter: int = 100000, stream=None):
+        """LAM = A^{-dagger} G (gamma5 A(-mu)^{-1} gamma5 G) for every column of G."""
+        nrhs = self._nrhs(G)
+        sts = (WdStats * nrhs)()
+        rc = lib().dbicgstab_solve_adjoint(
+            self._h, deflation._d if deflation is not None else None, _ptr(G), _ptr(LAM), nrhs,
+            float(tol), int(max_iter), sts, _stream(stream, G, LAM))
+        check(rc, allow=(_lib.WD_OK, _lib.WD_NOT_CONVERGED, _lib.WD_BREAKDOWN))
+        return rc, [s.as_dict() for s in sts]
+
+    def gradients(self, lam, x, force=None, want_dkappa: bool = True, stream=None):
+        """Link force (into `force`, V*4*8 float64 CUDA tensor) and dL/dkappa for
+        dL = Re(g^dagger dx), lam = A^{-dagger} g.  Returns dL/dkappa or None."""
+        dk = ctypes.c_double(0.0)
+        if force is not None and (str(force.dtype) != "torch.float64" or not force.is_contiguous()):
+            raise TypeError("force must be a contiguous float64 tensor")
+        check(lib().wd_gradients(self._h, _ptr(lam), _ptr(x),
+                                 force.data_ptr() if force is not None else None,
+                                 ctypes.byref(dk) if want_dkappa else None,
+                                 _stream(stream, lam, x)))
+        return dk.value if want_dkappa else None
+
+    def multishift(self, B, X, mus: Sequence[float], tol: float = 1e-10, max_iter: int = 100000,
+                   project: bool = True, mixed: bool = False, stream=None):
+        """Sec. 4: A(mu_i) X[i] = B for the shifts in the given order, each
+        projected over the earlier solutions.  X holds len(mus)*nrhs*12V
+        complex128 ([shift][rhs][...]).  Returns (status, stats [shift][rhs])."""
+        nrhs = self._nrhs(B)
+        ns = len(mus)
+        if _numel(X) != ns * _numel(B):
+            raise ValueError("X must hold len(mus) * nrhs vectors")
+        sts = (WdStats * (ns * nrhs))()
+        arr = (ctypes.c_double * ns)(*[float(m) for m in mus])
+        rc = lib().tm_multishift_solve(self._h, _ptr(B), _ptr(X), nrhs, arr, ns, float(tol),
+                                       int(max_iter), 1 if project else 0, 1 if mixed else 0,
+                                       sts, _stream(stream, B, X))
+        check(rc, allow=(_lib.WD_OK, _lib.WD_NOT_CONVERGED, _lib.WD_BREAKDOWN))
+        out = [s.as_dict() for s in sts]
+        return rc, [out[i * nrhs:(i + 1) * nrhs] for i in range(ns)]
+
+    def apply_f32(self, x, out, dagger: bool = False, stream=None):
+        """out = A x with the FP32 kernel (FP64 vectors rounded on entry)."""
+        nrhs = self._nrhs(x)
+        check(lib().wd_apply_f32(self._h, _ptr(x), _ptr(out), nrhs, 1 if dagger else 0,
+                                 _stream(stream, x, out)))
+        return out
 
     def dbicgstab_oneshot(self, B, X, V=None, k: int = 0, U=None, tol: float = 1e-10,
                           max_iter: int = 100000, stream=None):

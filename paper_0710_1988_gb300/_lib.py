@@ -62,12 +62,20 @@ D = ctypes.c_double
 SIGNATURES = {
     "wd_create": (I, [ctypes.POINTER(I), P, D, D, ctypes.POINTER(P)]),
     "wd_set_params": (I, [P, D, D]),
+    "wd_set_operator": (I, [P, I]),
+    "wd_eo_prepare": (I, [P, P, P, I, P]),
+    "wd_eo_reconstruct": (I, [P, P, P, P, I, P]),
     "wd_apply": (I, [P, P, P, I, I, P]),
     "gmresdr_solve": (I, [P, P, P, I, I, D, I, P, P, P, ctypes.POINTER(WdStats), P]),
     "wd_deflation_create": (I, [P, P, P, I, ctypes.POINTER(P), P]),
     "wd_deflation_destroy": (None, [P]),
     "dbicgstab_solve_deflated": (I, [P, P, P, P, I, D, I, ctypes.POINTER(WdStats), P]),
     "dbicgstab_solve": (I, [P, P, P, I, P, P, I, D, I, ctypes.POINTER(WdStats), P]),
+    "dbicgstab_solve_adjoint": (I, [P, P, P, P, I, D, I, ctypes.POINTER(WdStats), P]),
+    "wd_gradients": (I, [P, P, P, P, ctypes.POINTER(D), P]),
+    "tm_multishift_solve": (I, [P, P, P, I, ctypes.POINTER(D), I, D, I, I, I, ctypes.POINTER(WdStats), P]),
+    "dbicgstab_solve_mixed": (I, [P, P, P, P, I, D, I, I, ctypes.POINTER(WdStats), P]),
+    "wd_apply_f32": (I, [P, P, P, I, I, P]),
     "wd_profile_enable": (I, [P, ctypes.c_uint]),
     "wd_profile_read": (I, [P, ctypes.POINTER(WdProfile)]),
     "wd_destroy": (None, [P]),

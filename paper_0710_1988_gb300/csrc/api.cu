@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "mixed.h"
 #include "solvers.h"
 #include "wd_internal.h"
 
@@ -130,6 +131,12 @@ extern "C" int wd_create(const int lat[4], const void *links, double kappa, doub
   if (V * 12 >= (1LL << 40)) return bad("wd_create: lattice too large");
   wd_context *h = new wd_context();
   h->prof.d_sites = nullptr;
+  h->links32 = nullptr;
+  h->side = nullptr;
+  h->ev_in = h->ev_out = nullptr;
+  h->eo = 0;
+  h->eo_tmp = nullptr;
+  h->eo_tmp_cap = 0;
   for (int i = 0; i < 4; ++i) h->dims[i] = lat[i];
   h->V = V;
   h->n = 12 * V;
@@ -167,6 +174,55 @@ extern "C" int wd_create(const int lat[4], const void *links, double kappa, doub
   return WD_OK;
 }
 
+extern "C" int wd_set_operator(wd_handle h, int even_odd) {
+  if (h == nullptr) return bad("wd_set_operator: NULL handle");
+  if (even_odd && (h->dims[0] % 2 != 0)) return bad("wd_set_operator: even-odd needs an even Lx");
+  if (even_odd && (h->dims[1] % 2 || h->dims[2] % 2 || h->dims[3] % 2))
+    return bad("wd_set_operator: even-odd needs even extents (periodic parity)");
+  h->eo = even_odd ? 1 : 0;
+  return WD_OK;
+}
+
+extern "C" int wd_eo_prepare(wd_handle h, const void *B, void *Bhat, int nrhs, wd_stream stream) {
+  ProfScope prof_scope_(h ? &h->prof : nullptr);
+  if (h == nullptr || B == nullptr || Bhat == nullptr) return bad("wd_eo_prepare: NULL argument");
+  if (!h->eo) return bad("wd_eo_prepare: the handle is not in even-odd mode");
+  if (nrhs < 1 || nrhs > 65535) return bad("wd_eo_prepare: nrhs must be in [1, 65535]");
+  if (!is_device_pointer(B) || !is_device_pointer(Bhat)) return bad("wd_eo_prepare: device pointers required");
+  cudaStream_t s = (cudaStream_t)stream;
+  Arena ar;
+  ar.pool = h->pool;
+  ar.stream = s;
+  const size_t half = (size_t)nrhs * (h->n / 2);
+  double2 *be = ar.take<double2>(half), *bo = ar.take<double2>(half);
+  if (ar.failed) return bad_alloc();
+  cudaError_t e = launch_eo_prepare(h, static_cast<const double2 *>(B), static_cast<double2 *>(Bhat),
+                                    be, bo, nrhs, s);
+  ar.release();
+  return e == cudaSuccess ? WD_OK : cuda_fail(e, "wd_eo_prepare");
+}
+
+extern "C" int wd_eo_reconstruct(wd_handle h, const void *B, const void *Xe, void *X, int nrhs,
+                                 wd_stream stream) {
+  ProfScope prof_scope_(h ? &h->prof : nullptr);
+  if (h == nullptr || B == nullptr || Xe == nullptr || X == nullptr) return bad("wd_eo_reconstruct: NULL argument");
+  if (!h->eo) return bad("wd_eo_reconstruct: the handle is not in even-odd mode");
+  if (nrhs < 1 || nrhs > 65535) return bad("wd_eo_reconstruct: nrhs must be in [1, 65535]");
+  if (!is_device_pointer(B) || !is_device_pointer(Xe) || !is_device_pointer(X))
+    return bad("wd_eo_reconstruct: device pointers required");
+  cudaStream_t s = (cudaStream_t)stream;
+  Arena ar;
+  ar.pool = h->pool;
+  ar.stream = s;
+  const size_t half = (size_t)nrhs * (h->n / 2);
+  double2 *be = ar.take<double2>(half), *bo = ar.take<double2>(half);
+  if (ar.failed) return bad_alloc();
+  cudaError_t e = launch_eo_reconstruct(h, static_cast<const double2 *>(B), static_cast<const double2 *>(Xe),
+                                        static_cast<double2 *>(X), be, bo, nrhs, s);
+  ar.release();
+  return e == cudaSuccess ? WD_OK : cuda_fail(e, "wd_eo_reconstruct");
+}
+
 extern "C" int wd_set_params(wd_handle h, double kappa, double mu) {
   if (h == nullptr) return bad("wd_set_params: NULL handle");
   h->kappa = kappa;
@@ -178,6 +234,11 @@ extern "C" void wd_destroy(wd_handle h) {
   if (h == nullptr) return;
   cudaDeviceSynchronize();
   h->prof.destroy();
+  if (h->links32) cudaFree(h->links32);
+  if (h->eo_tmp) cudaFree(h->eo_tmp);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
   if (h->links) cudaFree(h->links);
   if (h->pool) cudaMemPoolDestroy(h->pool);
   delete h;
@@ -215,7 +276,7 @@ extern "C" int wd_apply(wd_handle h, const void *in, void *out, int nrhs, int da
     return bad("wd_apply: in and out must be device pointers");
   const char *a = static_cast<const char *>(in);
   const char *b = static_cast<const char *>(out);
-  const size_t bytes = sizeof(double2) * (size_t)h->n * nrhs;
+  const size_t bytes = sizeof(double2) * (size_t)op_n(h) * nrhs;
   if (a < b + bytes && b < a + bytes) return bad("wd_apply: in and out overlap");
   cudaError_t e = launch_wilson_f64(h, static_cast<const double2 *>(in),
                                     static_cast<double2 *>(out), nrhs, dagger ? 1 : 0,
@@ -234,7 +295,7 @@ extern "C" int gmresdr_solve(wd_handle h, const void *b, void *x, int m, int k, 
   if (b == nullptr || x == nullptr) return bad("gmresdr_solve: NULL b or x");
   if (m < 1 || m > 80) return bad("gmresdr_solve: m must be in [1, 80]");
   if (k < 0 || k >= m) return bad("gmresdr_solve: k must satisfy 0 <= k < m");
-  if ((long long)m > h->n) return bad("gmresdr_solve: m exceeds the vector length");
+  if ((long long)m > op_n(h)) return bad("gmresdr_solve: m exceeds the vector length");
   if (!(tol > 0.0)) return bad("gmresdr_solve: tol must be positive");
   if (max_mv < m) return bad("gmresdr_solve: max_mv must be >= m");
   if (V_out != nullptr && !is_device_pointer(V_out)) return bad("gmresdr_solve: V_out must be device memory");
@@ -246,7 +307,7 @@ extern "C" int gmresdr_solve(wd_handle h, const void *b, void *x, int m, int k, 
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, s);
-  const size_t bytes = sizeof(double2) * (size_t)h->n;
+  const size_t bytes = sizeof(double2) * (size_t)op_n(h);
   Staged sb, sx;
   int rc = stage_in(b, bytes, true, sb, ar, s);
   if (rc == WD_OK) rc = stage_in(x, bytes, true, sx, ar, s);
@@ -285,7 +346,7 @@ extern "C" int wd_deflation_create(wd_handle h, const void *V, const void *U, in
   if (!is_device_pointer(V) || (U != nullptr && !is_device_pointer(U)))
     return bad("wd_deflation_create: V and U must be device memory");
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t vb = sizeof(double2) * (size_t)h->n * k;
+  const size_t vb = sizeof(double2) * (size_t)op_n(h) * k;
   wd_deflation_space *d = new wd_deflation_space();
   std::memset(d, 0, sizeof(*d));
   d->h = h;
@@ -343,7 +404,7 @@ extern "C" int dbicgstab_solve_deflated(wd_handle h, wd_deflation d, const void 
   if (d != nullptr && (d->kappa != h->kappa || d->mu != h->mu))
     return bad("dbicgstab_solve: kappa/mu changed since the deflation space was built");
   cudaStream_t s = (cudaStream_t)stream;
-  const long long n = h->n;
+  const long long n = op_n(h);
   Arena ar;
   ar.pool = h->pool;
   ar.stream = s;
@@ -419,6 +480,229 @@ extern "C" int dbicgstab_solve(wd_handle h, const void *B, void *X, int nrhs, co
   int rc = dbicgstab_solve_deflated(h, d, B, X, nrhs, tol, max_iter, stats, stream);
   if (d) wd_deflation_destroy(d);
   return rc;
+}
+
+// ------------------------------------------------------------------ Sec. 4 shifts
+
+extern "C" int tm_multishift_solve(wd_handle h, const void *B, void *X, int nrhs,
+                                   const double *mus, int nshift, double tol, int max_iter,
+                                   int project, int mixed, wd_stats *stats, wd_stream stream) {
+  ProfScope prof_scope_(h ? &h->prof : nullptr);
+  if (h == nullptr) return bad("tm_multishift_solve: NULL handle");
+  if (B == nullptr || X == nullptr || mus == nullptr) return bad("tm_multishift_solve: NULL argument");
+  if (nrhs < 1 || nrhs > 65535) return bad("tm_multishift_solve: nrhs must be in [1, 65535]");
+  if (nshift < 1 || nshift > 64) return bad("tm_multishift_solve: nshift must be in [1, 64]");
+  if (!(tol > 0.0) || max_iter < 1) return bad("tm_multishift_solve: tol > 0 and max_iter >= 1 required");
+  if (!is_device_pointer(B) || !is_device_pointer(X)) return bad("tm_multishift_solve: B and X must be device memory");
+  cudaStream_t s = (cudaStream_t)stream;
+  Arena ar;
+  ar.pool = h->pool;
+  ar.stream = s;
+  int rc = tm_shifts_run(h, static_cast<const double2 *>(B), static_cast<double2 *>(X), nrhs, mus,
+                         nshift, tol, max_iter, project, mixed, stats, s, ar);
+  ar.release();
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess && rc != WD_CUDA_ERROR) rc = cuda_fail(e, "tm_multishift_solve");
+  return rc;
+}
+
+// ------------------------------------------------------------------ differentiation
+
+extern "C" int dbicgstab_solve_adjoint(wd_handle h, wd_deflation d, const void *G, void *LAM,
+                                       int nrhs, double tol, int max_iter, wd_stats *stats,
+                                       wd_stream stream) {
+  if (h == nullptr || G == nullptr || LAM == nullptr) return bad("dbicgstab_solve_adjoint: NULL argument");
+  if (nrhs < 1 || nrhs > 65535) return bad("dbicgstab_solve_adjoint: nrhs must be in [1, 65535]");
+  if (!is_device_pointer(G) || !is_device_pointer(LAM)) return bad("dbicgstab_solve_adjoint: G and LAM must be device memory");
+  if (G == LAM) return bad("dbicgstab_solve_adjoint: G and LAM must not alias");
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long nn = op_n(h) * nrhs;
+  Arena ar;
+  ar.pool = h->pool;
+  ar.stream = s;
+  double2 *t = ar.take<double2>((size_t)nn);
+  if (ar.failed) return bad_alloc();
+  cudaError_t e = launch_gamma5(static_cast<const double2 *>(G), t, nn, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(LAM, 0, sizeof(double2) * nn, s);
+  if (e != cudaSuccess) {
+    ar.release();
+    return cuda_fail(e, "dbicgstab_solve_adjoint");
+  }
+  const double mu = h->mu;
+  h->mu = -mu;
+  int rc = dbicgstab_solve_deflated(h, d, t, LAM, nrhs, tol, max_iter, stats, stream);
+  h->mu = mu;
+  if (rc == WD_OK || rc == WD_NOT_CONVERGED || rc == WD_BREAKDOWN) {
+    e = cudaMemcpyAsync(t, LAM, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = launch_gamma5(t, static_cast<double2 *>(LAM), nn, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "dbicgstab_solve_adjoint");
+  }
+  ar.release();
+  cudaStreamSynchronize(s);
+  return rc;
+}
+
+extern "C" int wd_gradients(wd_handle h, const void *lam, const void *x, void *force,
+                            double *dkappa, wd_stream stream) {
+  ProfScope prof_scope_(h ? &h->prof : nullptr);
+  if (h == nullptr || lam == nullptr || x == nullptr) return bad("wd_gradients: NULL argument");
+  if (h->eo) return bad("wd_gradients: defined for the full operator (wd_set_operator(h, 0))");
+  if (!is_device_pointer(lam) || !is_device_pointer(x) || (force && !is_device_pointer(force)))
+    return bad("wd_gradients: lam, x and force must be device memory");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (force) e = launch_link_force(h, static_cast<const double2 *>(lam), static_cast<const double2 *>(x),
+                                   static_cast<double *>(force), s);
+  if (e != cudaSuccess) return cuda_fail(e, "wd_gradients: force");
+  if (dkappa) {
+    if (h->kappa == 0.0) return bad("wd_gradients: dL/dkappa needs kappa != 0");
+    const long long n = h->n;
+    Arena ar;
+    ar.pool = h->pool;
+    ar.stream = s;
+    double2 *ax = ar.take<double2>((size_t)n);
+    double *part = ar.take<double>((size_t)stream_blocks(n));
+    if (ar.failed) return bad_alloc();
+    e = launch_wilson_f64(h, static_cast<const double2 *>(x), ax, 1, 0, s);
+    if (e == cudaSuccess)
+      e = launch_dkappa(static_cast<const double2 *>(lam), static_cast<const double2 *>(x), ax, h->mu,
+                        n, part, s);
+    std::vector<double> hp(stream_blocks(n));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hp.data(), part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, s);
+    ar.release();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "wd_gradients: dkappa");
+    double acc = 0.0;
+    for (double v : hp) acc += v;
+    *dkappa = acc / h->kappa;
+  }
+  return WD_OK;
+}
+
+// ------------------------------------------------------------------ mixed precision
+
+extern "C" int dbicgstab_solve_mixed(wd_handle h, wd_deflation d, const void *B, void *X,
+                                     int nrhs, double tol, int max_iter, int reliable_every,
+                                     wd_stats *stats, wd_stream stream) {
+  ProfScope prof_scope_(h ? &h->prof : nullptr);
+  if (h == nullptr) return bad("dbicgstab_solve_mixed: NULL handle");
+  if (h->eo) return bad("dbicgstab_solve_mixed: the FP32 path acts on the full operator");
+  if (B == nullptr || X == nullptr) return bad("dbicgstab_solve_mixed: NULL B or X");
+  if (nrhs < 1 || nrhs > 65535) return bad("dbicgstab_solve_mixed: nrhs must be in [1, 65535]");
+  if (!(tol > 0.0)) return bad("dbicgstab_solve_mixed: tol must be positive");
+  if (max_iter < 1 || reliable_every < 1) return bad("dbicgstab_solve_mixed: max_iter, reliable_every >= 1");
+  if (d != nullptr && d->h != h) return bad("dbicgstab_solve_mixed: deflation space built for another handle");
+  if (d != nullptr && (d->kappa != h->kappa || d->mu != h->mu))
+    return bad("dbicgstab_solve_mixed: kappa/mu changed since the deflation space was built");
+  cudaStream_t caller = (cudaStream_t)stream;
+  // CUDA graphs cannot be captured on the legacy default stream: work on the
+  // handle's side stream, ordered after and before the caller's stream
+  cudaStream_t s = caller;
+  if (caller == nullptr) {
+    if (h->side == nullptr) {
+      cudaError_t e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming);
+      if (e != cudaSuccess) return cuda_fail(e, "dbicgstab_solve_mixed: side stream");
+    }
+    s = h->side;
+    cudaEventRecord(h->ev_in, caller);
+    cudaStreamWaitEvent(s, h->ev_in, 0);
+  }
+  const long long n = h->n;
+  Arena ar;
+  ar.pool = h->pool;
+  ar.stream = s;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  const size_t bytes = sizeof(double2) * (size_t)n * nrhs;
+  Staged sb, sx;
+  std::vector<wd_stats> local(nrhs);
+  std::memset(local.data(), 0, sizeof(wd_stats) * nrhs);
+  int rc = stage_in(B, bytes, true, sb, ar, s);
+  if (rc == WD_OK) rc = stage_in(X, bytes, true, sx, ar, s);
+  double2 *R0 = rc == WD_OK ? ar.take<double2>((size_t)n * nrhs) : nullptr;
+  double *part = rc == WD_OK ? ar.take<double>((size_t)stream_blocks(n) * 2 * nrhs) : nullptr;
+  if (rc == WD_OK && ar.failed) rc = bad_alloc();
+  if (rc == WD_OK) {
+    std::vector<double> hp((size_t)stream_blocks(n) * 2 * nrhs);
+    cudaError_t e = launch_norms(sx.dev, nullptr, part, n, nrhs, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hp.data(), part, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "dbicgstab_solve_mixed: ||x0||");
+    bool zero = true;
+    for (size_t i = 0; i < hp.size(); i += 2) zero &= hp[i] == 0.0;
+    if (rc == WD_OK) {
+      if (zero) {
+        e = cudaMemcpyAsync(R0, sb.dev, bytes, cudaMemcpyDeviceToDevice, s);
+      } else {
+        e = launch_wilson_f64(h, sx.dev, R0, nrhs, 0, s);
+        if (e == cudaSuccess) e = launch_sub_norm(R0, sb.dev, R0, nullptr, M_ALL, part, n, nrhs, s);
+        for (auto &q : local) q.mvp_extra += 1;
+      }
+      if (e != cudaSuccess) rc = cuda_fail(e, "dbicgstab_solve_mixed: r0");
+    }
+  }
+  if (rc == WD_OK && d != nullptr) rc = deflate_batched(d, sx.dev, R0, nrhs, s, ar);
+  if (rc == WD_OK)
+    rc = bicgstab_mixed_batched(h, sb.dev, sx.dev, R0, nrhs, tol, max_iter, reliable_every,
+                                local.data(), s, ar);
+  if ((rc == WD_OK || rc == WD_NOT_CONVERGED || rc == WD_BREAKDOWN) && sx.host) {
+    cudaError_t e = cudaMemcpyAsync(X, sx.dev, bytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "dbicgstab_solve_mixed: copy X");
+  }
+  cudaEventRecord(e1, s);
+  ar.release();
+  if (s != caller) {
+    cudaEventRecord(h->ev_out, s);
+    cudaStreamWaitEvent(caller, h->ev_out, 0);
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess && rc != WD_CUDA_ERROR) rc = cuda_fail(e, "dbicgstab_solve_mixed");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (stats) {
+    for (int q = 0; q < nrhs; ++q) {
+      local[q].ms = ms;
+      stats[q] = local[q];
+    }
+  }
+  return rc;
+}
+
+extern "C" int wd_apply_f32(wd_handle h, const void *in, void *out, int nrhs, int dagger,
+                            wd_stream stream) {
+  ProfScope prof_scope_(h ? &h->prof : nullptr);
+  if (h == nullptr) return bad("wd_apply_f32: NULL handle");
+  if (h->eo) return bad("wd_apply_f32: the FP32 kernel acts on the full operator");
+  if (in == nullptr || out == nullptr) return bad("wd_apply_f32: NULL vector");
+  if (nrhs < 1 || nrhs > 65535) return bad("wd_apply_f32: nrhs must be in [1, 65535]");
+  if (!is_device_pointer(in) || !is_device_pointer(out))
+    return bad("wd_apply_f32: in and out must be device pointers");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = ensure_links32(h, s);
+  if (rc != WD_OK) return rc;
+  Arena ar;
+  ar.pool = h->pool;
+  ar.stream = s;
+  const size_t v32 = (size_t)nrhs * 6 * h->V;
+  float4 *a = ar.take<float4>(v32), *b = ar.take<float4>(v32);
+  if (ar.failed) return bad_alloc();
+  const Mixed32 m{h, h->links32};
+  cudaError_t e = launch_f64_to_f32(static_cast<const double2 *>(in), a, h->V, nrhs, nullptr,
+                                    nullptr, nullptr, M_ALL, s);
+  if (e == cudaSuccess)
+    e = launch_wilson_f32(m, a, nullptr, b, nrhs, dagger ? 1 : 0, EPI_NONE, nullptr, nullptr,
+                          nullptr, nullptr, M_ALL, s);
+  if (e == cudaSuccess) e = launch_f32_to_f64(b, static_cast<double2 *>(out), h->V, nrhs, s);
+  ar.release();
+  if (e != cudaSuccess) return cuda_fail(e, "wd_apply_f32");
+  return WD_OK;
 }
 
 // ------------------------------------------------------------------ errors

@@ -324,172 +324,177 @@ cudaError_t launch_bicg_finalize(int kind, const double *partial, int nb, BicgSc
 }
 
 // ----------------------------------------------------------------- tall-skinny
+//
+// Both products are FP64-ALU bound on this part (4 DFMA per complex
+// element pair against ~0.3 DFMA/byte of machine balance), so the kernels
+// are shaped to issue nothing but the DFMAs the product needs: every thread
+// walks vector elements, keeps a JT x RT (dot) or NC (update) tile of
+// complex accumulators in registers, and the block reduces once at the end.
 
 constexpr int TS_THREADS = 256;
-constexpr int TS_SLOTS = 8;     // (pair, split) work items per thread
 
-// Splits per output pair and elements per staged chunk for P = k*nrhs pairs:
-// S is the largest power of two with P*S <= TS_THREADS, the chunk holds
-// max(32, S) elements so that every split has work.
-static void ts_dot_shape(int P, int *S, int *CH) {
-  int sp = 1;
-  while (sp < 256 && P * sp * 2 <= TS_THREADS) sp *= 2;
-  *S = sp;
-  *CH = sp > 32 ? sp : 32;
+static void ts_dot_tile(int nrhs, int *JT, int *RT) {
+  *RT = nrhs >= 2 ? 2 : 1;
+  *JT = *RT == 1 ? 16 : 8;
+}
+
+static void ts_dot_grid(long long n, int k, int nrhs, dim3 *grid) {
+  int JT, RT;
+  ts_dot_tile(nrhs, &JT, &RT);
+  const int gy = (k + JT - 1) / JT, gz = (nrhs + RT - 1) / RT;
+  long long gx = TS_MAX_BLOCKS / (gy * gz);
+  const long long need = (n + TS_THREADS - 1) / TS_THREADS;
+  if (gx > need) gx = need;
+  if (gx < 8) gx = need < 8 ? need : 8;
+  if (gx < 1) gx = 1;
+  *grid = dim3((unsigned)gx, gy, gz);
 }
 
 int ts_dot_blocks(long long n, int k, int nrhs) {
-  int S, CH;
-  ts_dot_shape(k * nrhs, &S, &CH);
-  long long ch = (n + CH - 1) / CH;
-  long long b = ch < TS_MAX_BLOCKS ? ch : TS_MAX_BLOCKS;
-  return (int)(b < 1 ? 1 : b);
+  dim3 g;
+  ts_dot_grid(n, k, nrhs, &g);
+  return (int)(g.x * g.y * g.z);
 }
 
+template <int JT, int RT>
 __global__ void __launch_bounds__(TS_THREADS)
 ts_dot_kernel(const double2 *__restrict__ V, int k, const double2 *__restrict__ W, int nrhs,
-              int g5, long long n, int S, int CH, double2 *__restrict__ partial,
+              int g5, long long n, double2 *__restrict__ partial,
               const int *__restrict__ status) {
   if (status != nullptr && *status != 0) return;
-  extern __shared__ double2 sm[];
-  double2 *Vs = sm;                      // [k][CH]
-  double2 *Ws = sm + (size_t)k * CH;     // [nrhs][CH]
-  const int P = k * nrhs;
-  double2 acc[TS_SLOTS];
+  const int j0 = blockIdx.y * JT, r0 = blockIdx.z * RT;
+  const int nj = min(JT, k - j0), nr = min(RT, nrhs - r0);
+  double2 acc[JT][RT];
 #pragma unroll
-  for (int q = 0; q < TS_SLOTS; ++q) acc[q] = make_double2(0.0, 0.0);
-  const long long nch = (n + CH - 1) / CH;
-  for (long long ch = blockIdx.x; ch < nch; ch += gridDim.x) {
-    const long long i0 = ch * CH;
-    __syncthreads();
-    for (int e = threadIdx.x; e < (k + nrhs) * CH; e += blockDim.x) {
-      const int row = e / CH, col = e % CH;
-      const long long i = i0 + col;
-      double2 val = make_double2(0.0, 0.0);
-      if (i < n) {
-        if (row < k) {
-          val = V[(long long)row * n + i];
-        } else {
-          val = W[(long long)(row - k) * n + i];
-          if (g5 && (i % 12) >= 6) val = cneg(val);  // gamma5 = diag(1,1,-1,-1)
-        }
-      }
-      sm[(size_t)row * CH + col] = val;
+  for (int j = 0; j < JT; ++j)
+#pragma unroll
+    for (int r = 0; r < RT; ++r) acc[j][r] = make_double2(0.0, 0.0);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double2 w[RT];
+    const bool neg = g5 && (i % 12) >= 6;  // gamma5 = diag(1, 1, -1, -1)
+#pragma unroll
+    for (int r = 0; r < RT; ++r) {
+      w[r] = r < nr ? __ldg(W + (long long)(r0 + r) * n + i) : make_double2(0.0, 0.0);
+      if (neg) w[r] = cneg(w[r]);
     }
-    __syncthreads();
 #pragma unroll
-    for (int q = 0; q < TS_SLOTS; ++q) {
-      const int item = threadIdx.x + q * TS_THREADS;
-      if (item < P * S) {
-        const int pair = item / S, sp = item % S;
-        const int j = pair / nrhs, rr = pair % nrhs;
-        double2 a = acc[q];
-        for (int e = sp; e < CH; e += S) a = cfmac(Vs[j * CH + e], Ws[rr * CH + e], a);
-        acc[q] = a;
+    for (int j = 0; j < JT; ++j) {
+      if (j < nj) {
+        const double2 v = __ldg(V + (long long)(j0 + j) * n + i);
+#pragma unroll
+        for (int r = 0; r < RT; ++r) acc[j][r] = cfmac(v, w[r], acc[j][r]);
       }
     }
   }
-  // combine the splits of every pair in a fixed order
-  __syncthreads();
-  double2 *red = sm;  // [P][S]; the host sizes sm for max((k+nrhs)*CH, P*S)
+  // block reduction of the tile, fixed order
+  __shared__ double red[JT * RT * 2][TS_THREADS / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-  for (int q = 0; q < TS_SLOTS; ++q) {
-    const int item = threadIdx.x + q * TS_THREADS;
-    if (item < P * S) red[item] = acc[q];
-  }
+  for (int j = 0; j < JT; ++j)
+#pragma unroll
+    for (int r = 0; r < RT; ++r) {
+      double a = acc[j][r].x, b = acc[j][r].y;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, off);
+        b += __shfl_down_sync(0xffffffffu, b, off);
+      }
+      if (lane == 0) {
+        red[(j * RT + r) * 2][wid] = a;
+        red[(j * RT + r) * 2 + 1][wid] = b;
+      }
+    }
   __syncthreads();
-  for (int pair = threadIdx.x; pair < P; pair += blockDim.x) {
-    double2 t = make_double2(0.0, 0.0);
-    for (int sp = 0; sp < S; ++sp) t = cadd(t, red[pair * S + sp]);
-    partial[(long long)blockIdx.x * P + pair] = t;
+  const long long tile = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  for (int q = threadIdx.x; q < JT * RT; q += blockDim.x) {
+    double a = 0.0, b = 0.0;
+    for (int w2 = 0; w2 < TS_THREADS / 32; ++w2) {
+      a += red[q * 2][w2];
+      b += red[q * 2 + 1][w2];
+    }
+    partial[tile * JT * RT + q] = make_double2(a, b);
   }
 }
 
-__global__ void ts_dot_finalize_kernel(const double2 *__restrict__ partial, int nb, int k,
-                                       int nrhs, double2 *C, int ldc, double2 *C2, int ldc2,
-                                       const int *__restrict__ status) {
+__global__ void ts_dot_finalize_kernel(const double2 *__restrict__ partial, int gx, int gy,
+                                       int JT, int RT, int k, int nrhs, double2 *C, int ldc,
+                                       double2 *C2, int ldc2, const int *__restrict__ status) {
   if (status != nullptr && *status != 0) return;
   const int P = k * nrhs;
   for (int pair = blockIdx.x * blockDim.x + threadIdx.x; pair < P;
        pair += gridDim.x * blockDim.x) {
+    const int j = pair / nrhs, r = pair % nrhs;
+    const int ty = j / JT, jj = j % JT, tz = r / RT, rr = r % RT;
+    const long long base = ((long long)tz * gy + ty) * gx;
     double2 t = make_double2(0.0, 0.0);
-    for (int b = 0; b < nb; ++b) t = cadd(t, partial[(long long)b * P + pair]);
-    const int j = pair / nrhs, rr = pair % nrhs;
-    C[(long long)j * ldc + rr] = t;
+    for (int b = 0; b < gx; ++b) t = cadd(t, partial[(base + b) * JT * RT + jj * RT + rr]);
+    C[(long long)j * ldc + r] = t;
     if (C2 != nullptr) {
-      double2 &d = C2[(long long)j * ldc2 + rr];
+      double2 &d = C2[(long long)j * ldc2 + r];
       d = cadd(d, t);
     }
   }
 }
 
-static size_t ts_dot_smem(int k, int nrhs) {
-  int S, CH;
-  ts_dot_shape(k * nrhs, &S, &CH);
-  size_t a = (size_t)(k + nrhs) * CH;
-  size_t b = (size_t)k * nrhs * S;
-  return (a > b ? a : b) * sizeof(double2);
-}
-
 cudaError_t launch_ts_dot(const double2 *V, int k, const double2 *W, int nrhs, int g5,
                           long long n, double2 *partial, const int *status, cudaStream_t s) {
   ProfLaunch prof_(PC_TS, s);
-  if (k < 1 || nrhs < 1 || k * nrhs > TS_SLOTS * TS_THREADS || k + nrhs > TS_MAX_ROWS)
-    return cudaErrorInvalidValue;
-  int S, CH;
-  ts_dot_shape(k * nrhs, &S, &CH);
-  const size_t smem = ts_dot_smem(k, nrhs);
-  cudaError_t e = cudaFuncSetAttribute(ts_dot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(TS_MAX_ROWS * 32 * sizeof(double2)));
-  if (e != cudaSuccess) return e;
-  ts_dot_kernel<<<ts_dot_blocks(n, k, nrhs), TS_THREADS, smem, s>>>(V, k, W, nrhs, g5, n, S, CH,
-                                                                    partial, status);
+  if (k < 1 || nrhs < 1 || k > 4096 || nrhs > 4096) return cudaErrorInvalidValue;
+  dim3 grid;
+  ts_dot_grid(n, k, nrhs, &grid);
+  int JT, RT;
+  ts_dot_tile(nrhs, &JT, &RT);
+  if (RT == 1)
+    ts_dot_kernel<16, 1><<<grid, TS_THREADS, 0, s>>>(V, k, W, nrhs, g5, n, partial, status);
+  else
+    ts_dot_kernel<8, 2><<<grid, TS_THREADS, 0, s>>>(V, k, W, nrhs, g5, n, partial, status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_ts_dot_finalize(const double2 *partial, int nb, int k, int nrhs,
+cudaError_t launch_ts_dot_finalize(const double2 *partial, long long n, int k, int nrhs,
                                    double2 *C, int ldc, double2 *C2, int ldc2,
                                    const int *status, cudaStream_t s) {
   ProfLaunch prof_(PC_TS, s);
+  dim3 grid;
+  ts_dot_grid(n, k, nrhs, &grid);
+  int JT, RT;
+  ts_dot_tile(nrhs, &JT, &RT);
   const int P = k * nrhs;
-  ts_dot_finalize_kernel<<<(P + 127) / 128, 128, 0, s>>>(partial, nb, k, nrhs, C, ldc, C2, ldc2,
-                                                         status);
+  ts_dot_finalize_kernel<<<(P + 127) / 128, 128, 0, s>>>(partial, grid.x, grid.y, JT, RT, k, nrhs,
+                                                         C, ldc, C2, ldc2, status);
   return cudaGetLastError();
 }
 
-constexpr int TU_COLS = 16;
 constexpr int TU_THREADS = 256;
 constexpr int TU_MAXK = 128;
 
+template <int NC>
 __global__ void __launch_bounds__(TU_THREADS)
 ts_update_kernel(const double2 *__restrict__ V, int kv, const double2 *__restrict__ Y, int ldy,
-                 int ncol, const double2 *IN, double2 *OUT, int beta_one, double sign,
+                 int c0, const double2 *IN, double2 *OUT, int beta_one, double sign,
                  long long n, const int *__restrict__ status) {
   if (status != nullptr && *status != 0) return;
-  __shared__ double2 Ys[TU_MAXK * TU_COLS];
-  const int c0 = blockIdx.y * TU_COLS;
-  const int nc = min(TU_COLS, ncol - c0);
-  for (int e = threadIdx.x; e < kv * TU_COLS; e += blockDim.x) {
-    const int j = e / TU_COLS, c = e % TU_COLS;
-    Ys[e] = c < nc ? cscale(sign, Y[(long long)j * ldy + c0 + c]) : make_double2(0.0, 0.0);
+  __shared__ double2 Ys[TU_MAXK * NC];
+  for (int e = threadIdx.x; e < kv * NC; e += blockDim.x) {
+    const int j = e / NC, c = e % NC;
+    Ys[e] = cscale(sign, Y[(long long)j * ldy + c0 + c]);
   }
   __syncthreads();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    double2 acc[TU_COLS];
+    double2 acc[NC];
 #pragma unroll
-    for (int c = 0; c < TU_COLS; ++c) acc[c] = make_double2(0.0, 0.0);
+    for (int c = 0; c < NC; ++c) acc[c] = make_double2(0.0, 0.0);
     for (int j = 0; j < kv; ++j) {
-      const double2 v = V[(long long)j * n + i];
+      const double2 v = __ldg(V + (long long)j * n + i);
 #pragma unroll
-      for (int c = 0; c < TU_COLS; ++c) acc[c] = cfma(v, Ys[j * TU_COLS + c], acc[c]);
+      for (int c = 0; c < NC; ++c) acc[c] = cfma(v, Ys[j * NC + c], acc[c]);
     }
 #pragma unroll
-    for (int c = 0; c < TU_COLS; ++c) {
-      if (c < nc) {
-        const long long o = (long long)(c0 + c) * n + i;
-        OUT[o] = beta_one ? cadd(IN[o], acc[c]) : acc[c];
-      }
+    for (int c = 0; c < NC; ++c) {
+      const long long o = (long long)(c0 + c) * n + i;
+      OUT[o] = beta_one ? cadd(IN[o], acc[c]) : acc[c];
     }
   }
 }
@@ -501,10 +506,22 @@ cudaError_t launch_ts_update(const double2 *V, int kv, const double2 *Y, int ldy
   if (kv > TU_MAXK || kv < 1 || ncol < 1) return cudaErrorInvalidValue;
   long long blocks = (n + TU_THREADS - 1) / TU_THREADS;
   if (blocks > 1216) blocks = 1216;
-  dim3 grid((unsigned)blocks, (ncol + TU_COLS - 1) / TU_COLS);
-  ts_update_kernel<<<grid, TU_THREADS, 0, s>>>(V, kv, Y, ldy, ncol, IN, OUT, beta_one, sign, n,
-                                              status);
-  return cudaGetLastError();
+  for (int c0 = 0; c0 < ncol;) {
+    const int rem = ncol - c0;
+    const int nc = rem >= 16 ? 16 : rem >= 8 ? 8 : rem >= 4 ? 4 : rem >= 2 ? 2 : 1;
+    dim3 grid((unsigned)blocks);
+    switch (nc) {
+      case 16: ts_update_kernel<16><<<grid, TU_THREADS, 0, s>>>(V, kv, Y, ldy, c0, IN, OUT, beta_one, sign, n, status); break;
+      case 8: ts_update_kernel<8><<<grid, TU_THREADS, 0, s>>>(V, kv, Y, ldy, c0, IN, OUT, beta_one, sign, n, status); break;
+      case 4: ts_update_kernel<4><<<grid, TU_THREADS, 0, s>>>(V, kv, Y, ldy, c0, IN, OUT, beta_one, sign, n, status); break;
+      case 2: ts_update_kernel<2><<<grid, TU_THREADS, 0, s>>>(V, kv, Y, ldy, c0, IN, OUT, beta_one, sign, n, status); break;
+      default: ts_update_kernel<1><<<grid, TU_THREADS, 0, s>>>(V, kv, Y, ldy, c0, IN, OUT, beta_one, sign, n, status); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    c0 += nc;
+  }
+  return cudaSuccess;
 }
 
 // ----------------------------------------------------------------- Arnoldi helpers

@@ -19,7 +19,7 @@
 namespace wd {
 
 constexpr int LU_THREADS = 256;
-constexpr int CE_THREADS = 512;
+constexpr int CE_THREADS = 256;
 constexpr int CE_MAXM = 80;
 
 __device__ __forceinline__ double cabs1(double2 a) { return fabs(a.x) + fabs(a.y); }
@@ -138,7 +138,8 @@ __device__ int lu_factor_block(double2 *A, int ld, int k, int *piv) {
       singular = 1;
       continue;
     }
-    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) A[i * ld + j] = cdiv(A[i * ld + j], pv);
+    const double2 rp = cdiv(make_double2(1.0, 0.0), pv);
+    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) A[i * ld + j] = cmul(A[i * ld + j], rp);
     __syncthreads();
     const int w = k - j - 1;
     for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
@@ -306,23 +307,24 @@ __device__ void cycle_lsq(const CycleEndArgs &a, int me, double2 *sm) {
   __syncthreads();
 }
 
-// Complex Givens rotation G = [[c, s], [-conj(s), c]] with G [x; y] = [r; 0].
+// Complex Givens rotation G = [[c, s], [-conj(s), c]] with G [x; y] = [r; 0]:
+// c = |x| / nrm, s = (x / |x|) conj(y) / nrm, nrm = sqrt(|x|^2 + |y|^2).
 __device__ __forceinline__ void givens(double2 x, double2 y, double &c, double2 &s) {
-  const double ax = cabs_(x);
-  if (ax == 0.0) {
+  const double a2 = cnorm2(x), b2 = cnorm2(y);
+  if (a2 == 0.0) {
     c = 0.0;
     s = make_double2(1.0, 0.0);
     return;
   }
-  const double nrm = hypot(ax, cabs_(y));
-  c = ax / nrm;
-  s = cscale(1.0 / (ax * nrm), cmul(x, cconj(y)));
+  const double ra = rsqrt(a2), rn = rsqrt(a2 + b2);
+  c = a2 * ra * rn;
+  s = cscale(ra * rn, cmul(x, cconj(y)));
 }
 
 // Schur decomposition of the m x m matrix A (smem, row-major): on return
 // A holds upper triangular T and Z the unitary Schur vectors, A_in = Z T Z^dagger.
 // Returns 1 if the QR iteration did not converge in 30 m sweeps.
-__device__ int schur_block(double2 *A, double2 *Z, int m, double2 *u) {
+__device__ int schur_block(double2 *A, double2 *Z, int m, double2 *u, long long *clk) {
   const int tid = threadIdx.x, bd = blockDim.x;
   for (int e = tid; e < m * m; e += bd)
     Z[e] = (e / m == e % m) ? make_double2(1.0, 0.0) : make_double2(0.0, 0.0);
@@ -366,8 +368,17 @@ __device__ int schur_block(double2 *A, double2 *Z, int m, double2 *u) {
     __syncthreads();
   }
   const double anorm = part > 0.0 ? part : 1.0;
-  // shifted QR iteration
+  if (clk != nullptr && tid == 0) clk[7] = clock64();
+  // Shifted QR iteration.  Within a sweep only the active block
+  // [l..hi] x [l..hi] is updated rotation by rotation: thread 0 computes each
+  // rotation (and owns the two rows whose update feeds the next one), the
+  // block applies it, two barriers per rotation.  The parts of T outside the
+  // active block and the Schur vectors Z receive the sweep's rotations
+  // afterwards, one thread per row or column, without barriers.
+  __shared__ double s_gc[CE_MAXM];
+  __shared__ double2 s_gs[CE_MAXM];
   int hi = m - 1, its = 0, total = 0;
+  long long rotations = 0;
   while (hi > 0) {
     if (total >= 30 * m) return 1;
     int l = hi;
@@ -386,28 +397,33 @@ __device__ int schur_block(double2 *A, double2 *Z, int m, double2 *u) {
     }
     ++its;
     ++total;
-    const double2 a = A[(hi - 1) * m + hi - 1], b = A[(hi - 1) * m + hi];
-    const double2 c = A[hi * m + hi - 1], d = A[hi * m + hi];
-    double2 sigma;
-    if (its % 10 == 0) {
-      sigma = cadd(d, make_double2(cabs1(c), 0.0));  // exceptional shift
-    } else {  // eigenvalue of the trailing 2x2 block nearest to d
-      const double2 p = cscale(0.5, csub(a, d));
-      const double2 bc = cmul(b, c);
-      double2 q = csqrt_(cadd(cmul(p, p), bc));
-      if (p.x * q.x + p.y * q.y < 0.0) q = cneg(q);
-      const double2 den = cadd(p, q);
-      sigma = (den.x == 0.0 && den.y == 0.0) ? d : csub(d, cdiv(bc, den));
+    rotations += hi - l;
+    double2 x = make_double2(0.0, 0.0), y = make_double2(0.0, 0.0);
+    if (tid == 0) {
+      const double2 a = A[(hi - 1) * m + hi - 1], b = A[(hi - 1) * m + hi];
+      const double2 c = A[hi * m + hi - 1], d = A[hi * m + hi];
+      double2 sigma;
+      if (its % 10 == 0) {
+        sigma = cadd(d, make_double2(cabs1(c), 0.0));  // exceptional shift
+      } else {  // eigenvalue of the trailing 2x2 block nearest to d
+        const double2 p = cscale(0.5, csub(a, d));
+        const double2 bc = cmul(b, c);
+        double2 q = csqrt_(cadd(cmul(p, p), bc));
+        if (p.x * q.x + p.y * q.y < 0.0) q = cneg(q);
+        const double2 den = cadd(p, q);
+        sigma = (den.x == 0.0 && den.y == 0.0) ? d : csub(d, cdiv(bc, den));
+      }
+      x = csub(A[l * m + l], sigma);
+      y = A[(l + 1) * m + l];
+      givens(x, y, s_gc[l], s_gs[l]);
     }
-    double2 x = csub(A[l * m + l], sigma), y = A[(l + 1) * m + l];
-    __syncthreads();
     for (int kk = l; kk < hi; ++kk) {
-      double gc;
-      double2 gs;
-      givens(x, y, gc, gs);
+      __syncthreads();  // rotation kk published; previous column update done
+      const double gc = s_gc[kk];
+      const double2 gs = s_gs[kk];
       const double2 mgs = cneg(cconj(gs));
       const int c0 = kk > l ? kk - 1 : l;
-      for (int j = c0 + tid; j < m; j += bd) {
+      for (int j = c0 + tid; j <= hi; j += bd) {
         const double2 a1 = A[kk * m + j], a2 = A[(kk + 1) * m + j];
         A[kk * m + j] = cadd(cscale(gc, a1), cmul(gs, a2));
         A[(kk + 1) * m + j] = (kk > l && j == kk - 1) ? make_double2(0.0, 0.0)
@@ -416,20 +432,54 @@ __device__ int schur_block(double2 *A, double2 *Z, int m, double2 *u) {
       __syncthreads();
       const int rmax = kk + 2 < hi ? kk + 2 : hi;
       const double2 cgs = cconj(gs), ngs = cneg(gs);
-      for (int i = tid; i < rmax + 1 + m; i += bd) {
-        double2 *X = i <= rmax ? A : Z;
-        const int row = i <= rmax ? i : i - rmax - 1;
-        const double2 a1 = X[row * m + kk], a2 = X[row * m + kk + 1];
-        X[row * m + kk] = cadd(cscale(gc, a1), cmul(cgs, a2));
-        X[row * m + kk + 1] = cadd(cmul(ngs, a1), cscale(gc, a2));
+      // rows l..rmax of columns kk, kk+1; thread 0 takes rows kk+1 and kk+2
+      // (the next rotation's inputs) and then computes that rotation
+      if (tid == 0) {
+        // only the two entries the next rotation needs, then that rotation;
+        // threads >= 1 write the whole column update (the same values)
+        if (kk + 1 < hi) {
+          const double2 x1 = cadd(cscale(gc, A[(kk + 1) * m + kk]), cmul(cgs, A[(kk + 1) * m + kk + 1]));
+          const double2 y1 = cadd(cscale(gc, A[(kk + 2) * m + kk]), cmul(cgs, A[(kk + 2) * m + kk + 1]));
+          givens(x1, y1, s_gc[kk + 1], s_gs[kk + 1]);
+        }
+      } else {
+        for (int row = l + tid - 1; row <= rmax; row += bd - 1) {
+          const double2 a1 = A[row * m + kk], a2 = A[row * m + kk + 1];
+          A[row * m + kk] = cadd(cscale(gc, a1), cmul(cgs, a2));
+          A[row * m + kk + 1] = cadd(cmul(ngs, a1), cscale(gc, a2));
+        }
       }
-      __syncthreads();
-      if (kk < hi - 1) {
-        x = A[(kk + 1) * m + kk];
-        y = A[(kk + 2) * m + kk];
-      }
-      __syncthreads();
     }
+    __syncthreads();
+    // deferred: rows above the block (column rotations), columns right of it
+    // (row rotations), and the Schur vectors (column rotations)
+    for (int t = tid; t < l + (m - 1 - hi) + m; t += bd) {
+      if (t < l || t >= l + (m - 1 - hi)) {
+        double2 *X = t < l ? A : Z;
+        const int row = t < l ? t : t - l - (m - 1 - hi);
+        for (int kk = l; kk < hi; ++kk) {
+          const double gc = s_gc[kk];
+          const double2 gs = s_gs[kk];
+          const double2 a1 = X[row * m + kk], a2 = X[row * m + kk + 1];
+          X[row * m + kk] = cadd(cscale(gc, a1), cmul(cconj(gs), a2));
+          X[row * m + kk + 1] = cadd(cmul(cneg(gs), a1), cscale(gc, a2));
+        }
+      } else {
+        const int col = hi + 1 + (t - l);
+        for (int kk = l; kk < hi; ++kk) {
+          const double gc = s_gc[kk];
+          const double2 gs = s_gs[kk];
+          const double2 a1 = A[kk * m + col], a2 = A[(kk + 1) * m + col];
+          A[kk * m + col] = cadd(cscale(gc, a1), cmul(gs, a2));
+          A[(kk + 1) * m + col] = cadd(cmul(cneg(cconj(gs)), a1), cscale(gc, a2));
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (clk != nullptr && tid == 0) {
+    clk[8] = total;
+    clk[9] = rotations;
   }
   return 0;
 }
@@ -445,7 +495,11 @@ __global__ void __launch_bounds__(CE_THREADS) gmresdr_cycle_end_kernel(CycleEndA
     a.flags[0] = 0;
     a.flags[1] = me < m ? 1 : 0;
   }
+#define STAMP(i) \
+  if (a.clk != nullptr && tid == 0) a.clk[i] = clock64();
+  STAMP(0)
   cycle_lsq(a, me, sm);
+  STAMP(1)
   if (!a.do_restart || me < m) return;
   const double res = a.res[0];
   double2 *P = a.P;
@@ -471,14 +525,16 @@ __global__ void __launch_bounds__(CE_THREADS) gmresdr_cycle_end_kernel(CycleEndA
   lu_factor_block(Z, m, m, piv);
   __syncthreads();
   lu_solve_block(Z, m, piv, m, v1, 1, 1);
+  STAMP(2)
   const double hh = cnorm2(a.H[m * m + m - 1]);
   for (int i = tid; i < m; i += bd) A[i * m + m - 1] = cadd(A[i * m + m - 1], cscale(hh, v1[i]));
   __syncthreads();
-  if (schur_block(A, Z, m, v2)) {
+  if (schur_block(A, Z, m, v2, a.clk)) {
     if (tid == 0) a.flags[0] = 1;
     return;
   }
   __syncthreads();
+  STAMP(3)
   // order eigenvalues by (|theta|, Re, Im), index as the final tie-break
   for (int i = tid; i < m; i += bd) {
     const double2 ti = A[i * m + i];
@@ -544,6 +600,7 @@ __global__ void __launch_bounds__(CE_THREADS) gmresdr_cycle_end_kernel(CycleEndA
     }
   }
   __syncthreads();
+  STAMP(4)
   // P_k = QR of [g_1..g_k; 0] by Gram-Schmidt applied twice; p_{k+1} from rho
   double2 *coef = v2;
   for (int c = 0; c <= k; ++c) {
@@ -572,6 +629,7 @@ __global__ void __launch_bounds__(CE_THREADS) gmresdr_cycle_end_kernel(CycleEndA
     for (int i = tid; i <= m; i += bd) P[i * ldp + c] = nv > 0.0 ? cscale(1.0 / nv, v1[i]) : v1[i];
     __syncthreads();
   }
+  STAMP(5)
   // T1 = Hbar_m P_k ((m+1) x k) in the work buffer, then Hk = P^dagger T1, ck = P^dagger rho
   double2 *T1 = a.work + (size_t)m * k;
   for (int e = tid; e < (m + 1) * k; e += bd) {
@@ -593,6 +651,9 @@ __global__ void __launch_bounds__(CE_THREADS) gmresdr_cycle_end_kernel(CycleEndA
     a.ck[r] = s;
   }
   for (int q = tid; q < k; q += bd) a.theta[q] = A[sel[q] * m + sel[q]];
+  __syncthreads();
+  STAMP(6)
+#undef STAMP
 }
 
 size_t gmresdr_cycle_end_smem(int m) {

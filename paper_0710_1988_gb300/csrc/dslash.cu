@@ -17,54 +17,9 @@
 #include "cplx.cuh"
 #include "wd_internal.h"
 #include "kernels.cuh"
+#include "spin.cuh"
 
 namespace wd {
-
-// spinor component c = 3*sigma + a
-template <int MU, int S>  // S = -1: (1 - gamma_mu), S = +1: (1 + gamma_mu)
-__device__ __forceinline__ void project(const double2 (&p)[12], double2 (&h)[6]) {
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const double2 p0 = p[a], p1 = p[3 + a], p2 = p[6 + a], p3 = p[9 + a];
-    if (MU == 0) {        // B psi_dn = (-i p3, -i p2)
-      h[a] = S < 0 ? cadd(p0, cmuli(p3)) : csub(p0, cmuli(p3));
-      h[3 + a] = S < 0 ? cadd(p1, cmuli(p2)) : csub(p1, cmuli(p2));
-    } else if (MU == 1) { // B psi_dn = (-p3, p2)
-      h[a] = S < 0 ? cadd(p0, p3) : csub(p0, p3);
-      h[3 + a] = S < 0 ? csub(p1, p2) : cadd(p1, p2);
-    } else if (MU == 2) { // B psi_dn = (-i p2, i p3)
-      h[a] = S < 0 ? cadd(p0, cmuli(p2)) : csub(p0, cmuli(p2));
-      h[3 + a] = S < 0 ? csub(p1, cmuli(p3)) : cadd(p1, cmuli(p3));
-    } else {              // B psi_dn = (p2, p3)
-      h[a] = S < 0 ? csub(p0, p2) : cadd(p0, p2);
-      h[3 + a] = S < 0 ? csub(p1, p3) : cadd(p1, p3);
-    }
-  }
-}
-
-// acc += [chi ; S * B^dagger chi]
-template <int MU, int S>
-__device__ __forceinline__ void reconstruct(double2 (&acc)[12], const double2 (&c)[6]) {
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const double2 c0 = c[a], c1 = c[3 + a];
-    acc[a] = cadd(acc[a], c0);
-    acc[3 + a] = cadd(acc[3 + a], c1);
-    if (MU == 0) {        // B^dagger chi = (i c1, i c0)
-      acc[6 + a] = S < 0 ? csub(acc[6 + a], cmuli(c1)) : cadd(acc[6 + a], cmuli(c1));
-      acc[9 + a] = S < 0 ? csub(acc[9 + a], cmuli(c0)) : cadd(acc[9 + a], cmuli(c0));
-    } else if (MU == 1) { // B^dagger chi = (c1, -c0)
-      acc[6 + a] = S < 0 ? csub(acc[6 + a], c1) : cadd(acc[6 + a], c1);
-      acc[9 + a] = S < 0 ? cadd(acc[9 + a], c0) : csub(acc[9 + a], c0);
-    } else if (MU == 2) { // B^dagger chi = (i c0, -i c1)
-      acc[6 + a] = S < 0 ? csub(acc[6 + a], cmuli(c0)) : cadd(acc[6 + a], cmuli(c0));
-      acc[9 + a] = S < 0 ? cadd(acc[9 + a], cmuli(c1)) : csub(acc[9 + a], cmuli(c1));
-    } else {              // B^dagger chi = (c0, c1)
-      acc[6 + a] = S < 0 ? csub(acc[6 + a], c0) : cadd(acc[6 + a], c0);
-      acc[9 + a] = S < 0 ? csub(acc[9 + a], c1) : cadd(acc[9 + a], c1);
-    }
-  }
-}
 
 // chi = U h (ADJ = false) or U^dagger h (ADJ = true), two colour vectors
 template <bool ADJ>
@@ -121,21 +76,9 @@ wilson_f64_kernel(const double2 *__restrict__ links, const double2 *__restrict__
   const double2 *psi = in + (long long)r * 12 * g.V;
   double red[3] = {0.0, 0.0, 0.0};
   if (s < g.V) {
-    const int x = (int)(s % g.L[0]);
-    long long t1 = s / g.L[0];
-    const int y = (int)(t1 % g.L[1]);
-    t1 /= g.L[1];
-    const int z = (int)(t1 % g.L[2]);
-    const int t = (int)(t1 / g.L[2]);
-    const long long sx = 1, sy = g.L[0], sz = sy * g.L[1], st = sz * g.L[2];
-    const long long xp = x + 1 == g.L[0] ? s - (g.L[0] - 1) * sx : s + sx;
-    const long long xm = x == 0 ? s + (g.L[0] - 1) * sx : s - sx;
-    const long long yp = y + 1 == g.L[1] ? s - (g.L[1] - 1) * sy : s + sy;
-    const long long ym = y == 0 ? s + (g.L[1] - 1) * sy : s - sy;
-    const long long zp = z + 1 == g.L[2] ? s - (g.L[2] - 1) * sz : s + sz;
-    const long long zm = z == 0 ? s + (g.L[2] - 1) * sz : s - sz;
-    const long long tp = t + 1 == g.L[3] ? s - (g.L[3] - 1) * st : s + st;
-    const long long tm = t == 0 ? s + (g.L[3] - 1) * st : s - st;
+    const Nbrs nb = neighbours(s, g.L);
+    const long long xp = nb.up[0], xm = nb.dn[0], yp = nb.up[1], ym = nb.dn[1];
+    const long long zp = nb.up[2], zm = nb.dn[2], tp = nb.up[3], tm = nb.dn[3];
 
     constexpr int F = DAG ? +1 : -1;  // projector sign on forward hops
     constexpr int B = -F;             // and on backward hops
@@ -203,12 +146,21 @@ LatticeGeom geom_of(const wd_context *h) {
   return g;
 }
 
-int wilson_blocks(const wd_context *h) { return (int)((h->V + 127) / 128); }
+int eo_blocks(const wd_context *h);
+cudaError_t launch_schur_f64_epi(const wd_context *h, const double2 *in, double2 *out, int nrhs,
+                                 int dagger, int epi, const double2 *aux, double *partial,
+                                 const int *status, cudaStream_t s, unsigned mask);
+
+int wilson_blocks(const wd_context *h) {
+  return h->eo ? eo_blocks(h) : (int)((h->V + 127) / 128);
+}
 
 cudaError_t launch_wilson_f64_epi(const wd_context *h, const double2 *in, double2 *out,
                                   int nrhs, int dagger, int epi, const double2 *aux,
                                   double *partial, const int *status, cudaStream_t s,
                                   unsigned mask) {
+  if (h->eo)  // even-odd Schur operator on even half vectors
+    return launch_schur_f64_epi(h, in, out, nrhs, dagger, epi, aux, partial, status, s, mask);
   dim3 grid(wilson_blocks(h), nrhs);
   LatticeGeom g = geom_of(h);
   ProfLaunch prof(PC_DSLASH, s);

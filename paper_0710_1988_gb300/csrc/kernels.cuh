@@ -85,16 +85,20 @@ cudaError_t launch_bicg_finalize(int kind, const double *partial, int nb, BicgSc
 
 // ----------------------------------------------------------------- tall-skinny
 // C[j][r] = sum_i conj(V[j][i]) * (g5 ? gamma5 W[r] : W[r])[i],  j < k, r < nrhs.
-// Block partials (ts_dot_blocks of them, k*nrhs each) go to `partial`;
-// launch_ts_dot_finalize sums them in block order into C[j*ldc + r] and,
-// when C2 != nullptr, also adds them to C2[j*ldc2 + r].  k + nrhs <= 176.
-constexpr int TS_MAX_ROWS = 176;  // k + nrhs
-constexpr int TS_MAX_BLOCKS = 304;  // upper bound of ts_dot_blocks()
+// launch_ts_dot writes ts_dot_blocks(n, k, nrhs) tiles of block partials to
+// `partial` (k*nrhs complex per ... tile layout private to blas.cu, at most
+// TS_MAX_BLOCKS * 16 complex); launch_ts_dot_finalize, given the same
+// (n, k, nrhs), sums them in block order into C[j*ldc + r] and, when
+// C2 != nullptr, also adds them to C2[j*ldc2 + r].
+constexpr int TS_MAX_BLOCKS = 608;  // blocks of one ts_dot launch, all tiles
 int ts_dot_blocks(long long n, int k, int nrhs);
+inline size_t ts_dot_partial_count(long long n, int k, int nrhs) {
+  return (size_t)ts_dot_blocks(n, k, nrhs) * 16;  // JT*RT = 16 for every tile shape
+}
 cudaError_t launch_ts_dot(const double2 *V, int k, const double2 *W, int nrhs, int g5,
                           long long n, double2 *partial, const int *status,
                           cudaStream_t s);
-cudaError_t launch_ts_dot_finalize(const double2 *partial, int nb, int k, int nrhs,
+cudaError_t launch_ts_dot_finalize(const double2 *partial, long long n, int k, int nrhs,
                                    double2 *C, int ldc, double2 *C2, int ldc2,
                                    const int *status, cudaStream_t s);
 // OUT[c][i] = (beta_one ? IN[c][i] : 0) + sign * sum_j V[j][i] Y[j*ldy + c],
@@ -139,10 +143,27 @@ struct CycleEndArgs {
   double2 *ck;         // k+1: P^dagger rho
   double2 *theta;      // k harmonic Ritz values
   int *flags;          // [0] eig failure, [1] lucky
-  double2 *work;       // scratch >= 4*(m+1)*(m+1) complex
+  double2 *work;       // scratch >= 2*(m+1)*(m+1) complex
+  long long *clk;      // nullptr, or 10 slots: SM clock at phase boundaries, QR sweeps, rotations
   int do_restart;
 };
 cudaError_t launch_gmresdr_cycle_end(const CycleEndArgs &a, cudaStream_t s);
 size_t gmresdr_cycle_end_smem(int m);
+
+// ----------------------------------------------------------------- even-odd (evenodd.cu)
+// B full -> Bhat (even half); be, bo: scratch half vectors (nrhs each)
+cudaError_t launch_eo_prepare(wd_context *h, const double2 *B, double2 *Bhat, double2 *be,
+                              double2 *bo, int nrhs, cudaStream_t s);
+// B full, Xe even half -> X full
+cudaError_t launch_eo_reconstruct(wd_context *h, const double2 *B, const double2 *Xe, double2 *X,
+                                  double2 *be, double2 *bo, int nrhs, cudaStream_t s);
+
+// ----------------------------------------------------------------- gradients (force.cu)
+cudaError_t launch_link_force(const wd_context *h, const double2 *lam, const double2 *x, double *f,
+                              cudaStream_t s);
+// partial[b] (stream_blocks(n) of them) of Re sum conj(lam) (x + i mu g5 x - ax)
+cudaError_t launch_dkappa(const double2 *lam, const double2 *x, const double2 *ax, double mu,
+                          long long n, double *partial, cudaStream_t s);
+cudaError_t launch_gamma5(const double2 *in, double2 *out, long long n, cudaStream_t s);
 
 }  // namespace wd

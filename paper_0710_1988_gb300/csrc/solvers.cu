@@ -8,6 +8,9 @@
 //  deflation_build    W = A V, G = U^dagger A V, LU(G)         (Sec. 2)
 //  deflate_batched    y = G^{-1} U^dagger r0, x0 += V y, r0 -= W y (Sec. 2)
 //  gmresdr_run        GMRES-DR(m,k)                        (Sec. 1, Sec. 3)
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -40,7 +43,7 @@ int launch_ok(cudaError_t e, const char *what) {
 int bicgstab_batched(wd_context *h, const double2 *B, double2 *X, const double2 *R0,
                      int nrhs, double tol, int max_iter, wd_stats *stats, cudaStream_t s,
                      double *hist_host, int hist_len, Arena &ar) {
-  const long long n = h->n;
+  const long long n = op_n(h);
   const int nbs = stream_blocks(n), nbw = wilson_blocks(h);
   const size_t vec = (size_t)nrhs * n;
   double2 *r = ar.take<double2>(vec), *rhat = ar.take<double2>(vec);
@@ -143,20 +146,20 @@ int bicgstab_batched(wd_context *h, const double2 *B, double2 *X, const double2 
 
 int deflation_build(wd_deflation_space *d, cudaStream_t s, Arena &ar) {
   wd_context *h = d->h;
-  const long long n = h->n;
+  const long long n = op_n(h);
   const int k = d->k;
   // W = A V: k MVPs, batched as k right-hand sides
   RET_IF(launch_ok(launch_wilson_f64(h, d->V, d->W, k, 0, s), "wilson(V)"));
   // G = U^dagger W, in column groups of 16
   const double2 *Uop = d->U ? d->U : d->V;
   const int g5 = d->U ? 0 : 1;
-  double2 *part = ar.take<double2>((size_t)TS_MAX_BLOCKS * k * 16);
+  double2 *part = ar.take<double2>(ts_dot_partial_count(n, k, 16));
   double *info = ar.take<double>(2);
   if (ar.failed) return WD_OUT_OF_MEMORY;
   for (int j0 = 0; j0 < k; j0 += 16) {
     const int nc = k - j0 < 16 ? k - j0 : 16;
     RET_IF(launch_ok(launch_ts_dot(Uop, k, d->W + (size_t)j0 * n, nc, g5, n, part, nullptr, s), "ts_dot(G)"));
-    RET_IF(launch_ok(launch_ts_dot_finalize(part, ts_dot_blocks(n, k, nc), k, nc, d->LU + j0, k, nullptr, 0, nullptr, s), "ts_fin(G)"));
+    RET_IF(launch_ok(launch_ts_dot_finalize(part, n, k, nc, d->LU + j0, k, nullptr, 0, nullptr, s), "ts_fin(G)"));
   }
   RET_IF(launch_ok(launch_lu_factor(d->LU, k, d->piv, info, s), "lu_factor"));
   double hinfo[2];
@@ -172,20 +175,19 @@ int deflation_build(wd_deflation_space *d, cudaStream_t s, Arena &ar) {
 
 int deflate_batched(wd_deflation_space *d, double2 *X, double2 *R0, int nrhs, cudaStream_t s,
                     Arena &ar) {
-  const long long n = d->h->n;
+  const long long n = op_n(d->h);
   const int k = d->k;
   const double2 *Uop = d->U ? d->U : d->V;
   const int g5 = d->U ? 0 : 1;
   for (int r0 = 0; r0 < nrhs; r0 += 16) {
     const int nc = nrhs - r0 < 16 ? nrhs - r0 : 16;
-    const int nb = ts_dot_blocks(n, k, nc);
-    double2 *part = ar.take<double2>((size_t)nb * k * nc);
+    double2 *part = ar.take<double2>(ts_dot_partial_count(n, k, nc));
     double2 *C = ar.take<double2>((size_t)k * nc);
     if (ar.failed) return WD_OUT_OF_MEMORY;
     double2 *Xg = X + (size_t)r0 * n, *Rg = R0 + (size_t)r0 * n;
     // c = U^dagger r0 (= V^dagger gamma5 r0 when U = gamma5 V)
     RET_IF(launch_ok(launch_ts_dot(Uop, k, Rg, nc, g5, n, part, nullptr, s), "ts_dot(c)"));
-    RET_IF(launch_ok(launch_ts_dot_finalize(part, nb, k, nc, C, nc, nullptr, 0, nullptr, s), "ts_fin(c)"));
+    RET_IF(launch_ok(launch_ts_dot_finalize(part, n, k, nc, C, nc, nullptr, 0, nullptr, s), "ts_fin(c)"));
     // y = G^{-1} c
     RET_IF(launch_ok(launch_lu_solve(d->LU, d->piv, k, C, nc, s), "lu_solve"));
     // x0 += V y ; r0 -= W y  (W = A V, so r0 = b - A x0 stays exact)
@@ -200,13 +202,15 @@ int deflate_batched(wd_deflation_space *d, double2 *X, double2 *R0, int nrhs, cu
 int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, double tol,
                 int max_mv, double2 *V_out, double2 *Hbar_host, double2 *theta_host,
                 wd_stats *stats, cudaStream_t s, double *hist_host, int hist_len, Arena &ar) {
-  const long long n = h->n;
+  const long long n = op_n(h);
   const int nbs = stream_blocks(n), nbw = wilson_blocks(h);
   double2 *Va = ar.take<double2>((size_t)(m + 1) * n);
   double2 *Vb = ar.take<double2>((size_t)(m + 1) * n);
   double2 *w = ar.take<double2>(n);
   double2 *r = ar.take<double2>(n);
-  double2 *part_t = ar.take<double2>((size_t)TS_MAX_BLOCKS * (m + 1));
+  size_t npart = 0;
+  for (int j = 1; j <= m + 1; ++j) npart = std::max(npart, ts_dot_partial_count(n, j, 1));
+  double2 *part_t = ar.take<double2>(npart);
   double *part_w = ar.take<double>((size_t)nbw * 3);
   double *part_n = ar.take<double>((size_t)nbs * 2);
   double2 *H = ar.take<double2>((size_t)(m + 1) * m);
@@ -224,6 +228,9 @@ int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, doubl
   int *status = ar.take<int>(1);
   int *m_eff = ar.take<int>(1);
   double2 *work = ar.take<double2>((size_t)2 * (m + 1) * (m + 1));
+  // WD_TRACE_DENSE=1 prints the SM-clock split of every cycle-end kernel
+  const bool trace_dense = std::getenv("WD_TRACE_DENSE") != nullptr;
+  long long *clk = trace_dense ? ar.take<long long>(10) : nullptr;
   if (ar.failed) return WD_OUT_OF_MEMORY;
 
   long long mvp = 0, mvp_extra = 0;
@@ -271,10 +278,10 @@ int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, doubl
       RET_IF(launch_ok(launch_wilson_f64_epi(h, vj, w, 1, 0, EPI_TSTT, nullptr, part_w, status, s, M_ACTIVE), "arnoldi wilson"));
       // classical Gram-Schmidt, applied twice
       RET_IF(launch_ok(launch_ts_dot(V, j + 1, w, 1, 0, n, part_t, status, s), "cgs dot1"));
-      RET_IF(launch_ok(launch_ts_dot_finalize(part_t, ts_dot_blocks(n, j + 1, 1), j + 1, 1, H + j, m, nullptr, 0, status, s), "cgs fin1"));
+      RET_IF(launch_ok(launch_ts_dot_finalize(part_t, n, j + 1, 1, H + j, m, nullptr, 0, status, s), "cgs fin1"));
       RET_IF(launch_ok(launch_ts_update(V, j + 1, H + j, m, 1, w, w, 1, -1.0, n, status, s), "cgs upd1"));
       RET_IF(launch_ok(launch_ts_dot(V, j + 1, w, 1, 0, n, part_t, status, s), "cgs dot2"));
-      RET_IF(launch_ok(launch_ts_dot_finalize(part_t, ts_dot_blocks(n, j + 1, 1), j + 1, 1, h2, 1, H + j, m, status, s), "cgs fin2"));
+      RET_IF(launch_ok(launch_ts_dot_finalize(part_t, n, j + 1, 1, h2, 1, H + j, m, status, s), "cgs fin2"));
       RET_IF(launch_ok(launch_ts_update(V, j + 1, h2, 1, 1, w, w, 1, -1.0, n, status, s), "cgs upd2"));
       // h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}
       RET_IF(launch_ok(launch_norms(w, nullptr, part_n, n, 1, s), "norm w"));
@@ -286,7 +293,18 @@ int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, doubl
     a.H = H; a.c = c; a.m = m; a.k = k; a.m_eff = m_eff; a.d = d; a.rho = rho; a.res = res;
     a.P = P; a.Hk = Hk; a.ck = ck; a.theta = theta; a.flags = flags; a.work = work;
     a.do_restart = 1;
+    a.clk = clk;
     RET_IF(launch_ok(launch_gmresdr_cycle_end(a, s), "cycle_end"));
+    if (clk) {
+      long long hc[10] = {0};
+      WD_CK(cudaMemcpyAsync(hc, clk, sizeof(hc), cudaMemcpyDeviceToHost, s));
+      WD_CK(cudaStreamSynchronize(s));
+      std::fprintf(stderr,
+                   "cycle_end clk: lsq %lld lu %lld hessenberg %lld qr-iter %lld eigvec %lld "
+                   "qr(P) %lld products %lld | sweeps %lld rotations %lld\n",
+                   hc[1] - hc[0], hc[2] - hc[1], hc[7] - hc[2], hc[3] - hc[7], hc[4] - hc[3],
+                   hc[5] - hc[4], hc[6] - hc[5], hc[8], hc[9]);
+    }
     int hflags[2], hme;
     double hres;
     WD_CK(cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, s));
@@ -331,7 +349,7 @@ int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, doubl
       // re-orthogonalise v_{k+1} against v_1..v_k
       double2 *vk = V + (size_t)k * n;
       RET_IF(launch_ok(launch_ts_dot(V, k, vk, 1, 0, n, part_t, nullptr, s), "reorth dot"));
-      RET_IF(launch_ok(launch_ts_dot_finalize(part_t, ts_dot_blocks(n, k, 1), k, 1, h2, 1, nullptr, 0, nullptr, s), "reorth fin"));
+      RET_IF(launch_ok(launch_ts_dot_finalize(part_t, n, k, 1, h2, 1, nullptr, 0, nullptr, s), "reorth fin"));
       RET_IF(launch_ok(launch_ts_update(V, k, h2, 1, 1, vk, vk, 1, -1.0, n, nullptr, s), "reorth upd"));
       RET_IF(launch_ok(launch_norms(vk, nullptr, part_n, n, 1, s), "reorth norm"));
       RET_IF(launch_ok(launch_norm_finalize(part_n, nbs, 2, scal, s), "reorth nrm"));
@@ -362,6 +380,65 @@ int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, doubl
   if (hist_host) {
     for (int i = 0; i < hist_len && i < (int)hist.size(); ++i) hist_host[i] = hist[i];
   }
+  return rc;
+}
+
+// --------------------------------------------------------------------- Sec. 4 shifts
+
+// Twisted-mass systems A(mu_i) x_i = b solved one shift after another
+// (Sec. 4).  Before shift i, every right-hand side is projected over its own
+// solutions of shifts 0..i-1: with Q = [x_0 .. x_{i-1}], solve
+// Q^dagger A_i^dagger A_i Q d = Q^dagger A_i^dagger b and start from Q d.
+int tm_shifts_run(wd_context *h, const double2 *B, double2 *X, int nrhs, const double *mus,
+                  int nshift, double tol, int max_iter, int project, int mixed,
+                  wd_stats *stats, cudaStream_t s, Arena &ar) {
+  const long long n = op_n(h);
+  const double mu_saved = h->mu;
+  const int kmax = nshift > 1 ? nshift - 1 : 1;
+  double2 *R0 = ar.take<double2>((size_t)nrhs * n);
+  double2 *Qc = ar.take<double2>((size_t)kmax * n);
+  double2 *AQ = ar.take<double2>((size_t)kmax * n);
+  double2 *part = ar.take<double2>(ts_dot_partial_count(n, kmax, kmax));
+  double2 *M = ar.take<double2>((size_t)kmax * kmax);
+  double2 *c = ar.take<double2>(kmax);
+  int *piv = ar.take<int>(kmax);
+  double *info = ar.take<double>(2);
+  if (ar.failed) return WD_OUT_OF_MEMORY;
+  int rc = WD_OK;
+  for (int i = 0; i < nshift && rc != WD_CUDA_ERROR && rc != WD_OUT_OF_MEMORY; ++i) {
+    h->mu = mus[i];
+    double2 *Xi = X + (size_t)i * nrhs * n;
+    WD_CK(cudaMemcpyAsync(R0, B, sizeof(double2) * nrhs * n, cudaMemcpyDeviceToDevice, s));
+    WD_CK(cudaMemsetAsync(Xi, 0, sizeof(double2) * nrhs * n, s));
+    wd_stats *st = stats ? stats + (size_t)i * nrhs : nullptr;
+    if (st) std::memset(st, 0, sizeof(wd_stats) * nrhs);
+    if (project && i > 0) {
+      for (int r = 0; r < nrhs; ++r) {
+        for (int j = 0; j < i; ++j)
+          WD_CK(cudaMemcpyAsync(Qc + (size_t)j * n, X + ((size_t)j * nrhs + r) * n,
+                                sizeof(double2) * n, cudaMemcpyDeviceToDevice, s));
+        RET_IF(launch_ok(launch_wilson_f64(h, Qc, AQ, i, 0, s), "A Q"));
+        RET_IF(launch_ok(launch_ts_dot(AQ, i, AQ, i, 0, n, part, nullptr, s), "Q^H A^H A Q"));
+        RET_IF(launch_ok(launch_ts_dot_finalize(part, n, i, i, M, i, nullptr, 0, nullptr, s), "fin M"));
+        RET_IF(launch_ok(launch_ts_dot(AQ, i, B + (size_t)r * n, 1, 0, n, part, nullptr, s), "Q^H A^H b"));
+        RET_IF(launch_ok(launch_ts_dot_finalize(part, n, i, 1, c, 1, nullptr, 0, nullptr, s), "fin c"));
+        RET_IF(launch_ok(launch_lu_factor(M, i, piv, info, s), "lu"));
+        double hinfo[2];
+        WD_CK(cudaMemcpyAsync(hinfo, info, sizeof(hinfo), cudaMemcpyDeviceToHost, s));
+        WD_CK(cudaStreamSynchronize(s));
+        if (st) st[r].mvp_extra += i;
+        if (hinfo[0] != 0.0 || hinfo[1] > 1e14) continue;  // degenerate Q: start from 0
+        RET_IF(launch_ok(launch_lu_solve(M, piv, i, c, 1, s), "lu solve"));
+        RET_IF(launch_ok(launch_ts_update(Qc, i, c, 1, 1, nullptr, Xi + (size_t)r * n, 0, 1.0, n, nullptr, s), "x0 = Q d"));
+        RET_IF(launch_ok(launch_ts_update(AQ, i, c, 1, 1, B + (size_t)r * n, R0 + (size_t)r * n, 1, -1.0, n, nullptr, s), "r0 = b - A Q d"));
+      }
+    }
+    int rci = mixed ? bicgstab_mixed_batched(h, B, Xi, R0, nrhs, tol, max_iter, 50, st, s, ar)
+                    : bicgstab_batched(h, B, Xi, R0, nrhs, tol, max_iter, st, s, nullptr, 0, ar);
+    if (rci == WD_CUDA_ERROR || rci == WD_OUT_OF_MEMORY) rc = rci;
+    else if (rci != WD_OK && rc == WD_OK) rc = rci;
+  }
+  h->mu = mu_saved;
   return rc;
 }
 

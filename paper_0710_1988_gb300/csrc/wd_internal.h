@@ -75,7 +75,17 @@ struct wd_context {
   double2 *links;   // device, [V][4][3][3] complex128
   cudaMemPool_t pool;  // this handle's scratch pool
   wd::Profiler prof;   // optional kernel timing
+  float4 *links32;     // FP32 rows 0, 1 of every link (mixed precision), lazily built
+  cudaStream_t side;   // non-blocking stream for graph capture when the caller
+                       // passes the legacy default stream; lazily created
+  cudaEvent_t ev_in, ev_out;
+  int eo;              // 1: the operator is the even-odd Schur complement on even sites
+  double2 *eo_tmp;     // odd half-vector scratch of the Schur operator
+  size_t eo_tmp_cap;   // complex numbers
 };
+
+// Length (complex numbers) of the vectors the solvers work on.
+inline long long op_n(const wd_context *h) { return h->eo ? h->n / 2 : h->n; }
 
 struct wd_deflation_space {
   wd_context *h;
