@@ -22,6 +22,10 @@ constexpr int LU_THREADS = 256;
 constexpr int CE_THREADS = 256;
 constexpr int CE_MAXM = 80;
 
+// shared-memory leading dimension of an m-column complex matrix: the next
+// value = 1 (mod 8) at or above m
+__host__ __device__ inline int cyc_ld(int m) { return m + ((9 - m % 8) % 8); }
+
 __device__ __forceinline__ double cabs1(double2 a) { return fabs(a.x) + fabs(a.y); }
 
 __device__ double2 csqrt_(double2 z) {
@@ -257,12 +261,12 @@ __device__ void reflect_right(double2 *X, int ld, const double2 *u, double tau, 
 // row-major (m+1) x m Hbar.  Writes d (m entries, zero beyond me), rho = c - Hbar d
 // (m+1 entries) and ||rho||.
 __device__ void cycle_lsq(const CycleEndArgs &a, int me, double2 *sm) {
-  const int m = a.m, ld = m;
-  double2 *Hs = sm;                    // (m+1) x m
-  double2 *cz = Hs + (m + 1) * m;      // m+1
+  const int m = a.m, ld = cyc_ld(m);
+  double2 *Hs = sm;                    // (m+1) x ld
+  double2 *cz = Hs + (m + 1) * ld;     // m+1
   double2 *u = cz + (m + 1);           // m+1
   double2 *dd = u + (m + 1);           // m
-  for (int e = threadIdx.x; e < (m + 1) * m; e += blockDim.x) Hs[e] = a.H[e];
+  for (int e = threadIdx.x; e < (m + 1) * m; e += blockDim.x) Hs[(e / m) * ld + e % m] = a.H[e];
   for (int i = threadIdx.x; i <= m; i += blockDim.x) cz[i] = a.c[i];
   __syncthreads();
   for (int j = 0; j < me; ++j) {
@@ -298,7 +302,7 @@ __device__ void cycle_lsq(const CycleEndArgs &a, int me, double2 *sm) {
   double part = 0.0;
   for (int i = threadIdx.x; i <= m; i += blockDim.x) {
     double2 v = a.c[i];
-    for (int j = 0; j < me; ++j) v = csub(v, cmul(a.H[i * ld + j], dd[j]));
+    for (int j = 0; j < me; ++j) v = csub(v, cmul(a.H[i * m + j], dd[j]));
     a.rho[i] = v;
     part += cnorm2(v);
   }
@@ -324,35 +328,35 @@ __device__ __forceinline__ void givens(double2 x, double2 y, double &c, double2 
 // Schur decomposition of the m x m matrix A (smem, row-major): on return
 // A holds upper triangular T and Z the unitary Schur vectors, A_in = Z T Z^dagger.
 // Returns 1 if the QR iteration did not converge in 30 m sweeps.
-__device__ int schur_block(double2 *A, double2 *Z, int m, double2 *u, long long *clk) {
+__device__ int schur_block(double2 *A, double2 *Z, int m, int ld, double2 *u, long long *clk) {
   const int tid = threadIdx.x, bd = blockDim.x;
   for (int e = tid; e < m * m; e += bd)
-    Z[e] = (e / m == e % m) ? make_double2(1.0, 0.0) : make_double2(0.0, 0.0);
+    Z[(e / m) * ld + e % m] = (e / m == e % m) ? make_double2(1.0, 0.0) : make_double2(0.0, 0.0);
   __syncthreads();
   // Householder reduction to upper Hessenberg form
   for (int j = 0; j + 2 < m; ++j) {
     double part = 0.0;
-    for (int i = j + 2 + tid; i < m; i += bd) part += cnorm2(A[i * m + j]);
+    for (int i = j + 2 + tid; i < m; i += bd) part += cnorm2(A[i * ld + j]);
     const double below = block_dsum_all(part);
     if (below == 0.0) continue;
-    const double2 al = A[(j + 1) * m + j];
+    const double2 al = A[(j + 1) * ld + j];
     const double aa = cabs_(al), nx = sqrt(below + aa * aa);
     const double2 ph = aa > 0.0 ? cscale(1.0 / aa, al) : make_double2(1.0, 0.0);
     const double2 beta = cscale(-nx, ph);
-    for (int i = j + 1 + tid; i < m; i += bd) u[i] = i == j + 1 ? csub(al, beta) : A[i * m + j];
+    for (int i = j + 1 + tid; i < m; i += bd) u[i] = i == j + 1 ? csub(al, beta) : A[i * ld + j];
     __syncthreads();
     const double tau = 1.0 / (nx * (nx + aa));
-    reflect_left(A, m, u, tau, j + 1, m - 1, j, m);
+    reflect_left(A, ld, u, tau, j + 1, m - 1, j, m);
     __syncthreads();
-    reflect_right(A, m, u, tau, j + 1, m - 1, 0, m);
-    reflect_right(Z, m, u, tau, j + 1, m - 1, 0, m);
+    reflect_right(A, ld, u, tau, j + 1, m - 1, 0, m);
+    reflect_right(Z, ld, u, tau, j + 1, m - 1, 0, m);
     __syncthreads();
     for (int i = j + 1 + tid; i < m; i += bd)
-      A[i * m + j] = i == j + 1 ? beta : make_double2(0.0, 0.0);
+      A[i * ld + j] = i == j + 1 ? beta : make_double2(0.0, 0.0);
     __syncthreads();
   }
   double part = 0.0;
-  for (int e = tid; e < m * m; e += bd) part = fmax(part, cabs1(A[e]));
+  for (int e = tid; e < m * m; e += bd) part = fmax(part, cabs1(A[(e / m) * ld + e % m]));
   {
     __shared__ double smax[32];
     for (int off = 16; off > 0; off >>= 1) part = fmax(part, __shfl_down_sync(0xffffffffu, part, off));
@@ -370,25 +374,29 @@ __device__ int schur_block(double2 *A, double2 *Z, int m, double2 *u, long long 
   const double anorm = part > 0.0 ? part : 1.0;
   if (clk != nullptr && tid == 0) clk[7] = clock64();
   // Shifted QR iteration.  Within a sweep only the active block
-  // [l..hi] x [l..hi] is updated rotation by rotation: thread 0 computes each
-  // rotation (and owns the two rows whose update feeds the next one), the
-  // block applies it, two barriers per rotation.  The parts of T outside the
-  // active block and the Schur vectors Z receive the sweep's rotations
-  // afterwards, one thread per row or column, without barriers.
+  // [l..hi] x [l..hi] is updated rotation by rotation, two barriers per
+  // rotation.  Lane 0 of the last warp (rt) computes the shift and every
+  // rotation and owns the rows kk+1..kk+2 of each column update, whose new
+  // entries give the next rotation; the other warps update everything else.
+  // The parts of T outside the active block and the Schur vectors Z receive
+  // the sweep's rotations afterwards, one thread per row or column.
   __shared__ double s_gc[CE_MAXM];
   __shared__ double2 s_gs[CE_MAXM];
+  const int rt = bd - 32;   // rotation thread
+  const int nwk = bd - 32;  // threads of the bulk updates
+  long long rotations = 0, t_scan = 0, t_rot = 0, t_def = 0, t0 = 0;
   int hi = m - 1, its = 0, total = 0;
-  long long rotations = 0;
   while (hi > 0) {
     if (total >= 30 * m) return 1;
+    if (tid == 0) t0 = clock64();
     int l = hi;
     for (; l > 0; --l) {
-      double tst = cabs1(A[(l - 1) * m + l - 1]) + cabs1(A[l * m + l]);
+      double tst = cabs1(A[(l - 1) * ld + l - 1]) + cabs1(A[l * ld + l]);
       if (tst == 0.0) tst = anorm;
-      if (cabs1(A[l * m + l - 1]) <= 2.220446049250313e-16 * tst) break;
+      if (cabs1(A[l * ld + l - 1]) <= 2.220446049250313e-16 * tst) break;
     }
     __syncthreads();
-    if (l > 0 && tid == 0) A[l * m + l - 1] = make_double2(0.0, 0.0);
+    if (l > 0 && tid == 0) A[l * ld + l - 1] = make_double2(0.0, 0.0);
     __syncthreads();
     if (l == hi) {
       --hi;
@@ -398,10 +406,14 @@ __device__ int schur_block(double2 *A, double2 *Z, int m, double2 *u, long long 
     ++its;
     ++total;
     rotations += hi - l;
-    double2 x = make_double2(0.0, 0.0), y = make_double2(0.0, 0.0);
     if (tid == 0) {
-      const double2 a = A[(hi - 1) * m + hi - 1], b = A[(hi - 1) * m + hi];
-      const double2 c = A[hi * m + hi - 1], d = A[hi * m + hi];
+      const long long t1 = clock64();
+      t_scan += t1 - t0;
+      t0 = t1;
+    }
+    if (tid == rt) {
+      const double2 a = A[(hi - 1) * ld + hi - 1], b = A[(hi - 1) * ld + hi];
+      const double2 c = A[hi * ld + hi - 1], d = A[hi * ld + hi];
       double2 sigma;
       if (its % 10 == 0) {
         sigma = cadd(d, make_double2(cabs1(c), 0.0));  // exceptional shift
@@ -413,9 +425,7 @@ __device__ int schur_block(double2 *A, double2 *Z, int m, double2 *u, long long 
         const double2 den = cadd(p, q);
         sigma = (den.x == 0.0 && den.y == 0.0) ? d : csub(d, cdiv(bc, den));
       }
-      x = csub(A[l * m + l], sigma);
-      y = A[(l + 1) * m + l];
-      givens(x, y, s_gc[l], s_gs[l]);
+      givens(csub(A[l * ld + l], sigma), A[(l + 1) * ld + l], s_gc[l], s_gs[l]);
     }
     for (int kk = l; kk < hi; ++kk) {
       __syncthreads();  // rotation kk published; previous column update done
@@ -423,34 +433,38 @@ __device__ int schur_block(double2 *A, double2 *Z, int m, double2 *u, long long 
       const double2 gs = s_gs[kk];
       const double2 mgs = cneg(cconj(gs));
       const int c0 = kk > l ? kk - 1 : l;
-      for (int j = c0 + tid; j <= hi; j += bd) {
-        const double2 a1 = A[kk * m + j], a2 = A[(kk + 1) * m + j];
-        A[kk * m + j] = cadd(cscale(gc, a1), cmul(gs, a2));
-        A[(kk + 1) * m + j] = (kk > l && j == kk - 1) ? make_double2(0.0, 0.0)
-                                                       : cadd(cmul(mgs, a1), cscale(gc, a2));
+      if (tid < nwk) {
+        for (int j = c0 + tid; j <= hi; j += nwk) {
+          const double2 a1 = A[kk * ld + j], a2 = A[(kk + 1) * ld + j];
+          A[kk * ld + j] = cadd(cscale(gc, a1), cmul(gs, a2));
+          A[(kk + 1) * ld + j] = (kk > l && j == kk - 1) ? make_double2(0.0, 0.0)
+                                                         : cadd(cmul(mgs, a1), cscale(gc, a2));
+        }
       }
       __syncthreads();
       const int rmax = kk + 2 < hi ? kk + 2 : hi;
       const double2 cgs = cconj(gs), ngs = cneg(gs);
-      // rows l..rmax of columns kk, kk+1; thread 0 takes rows kk+1 and kk+2
-      // (the next rotation's inputs) and then computes that rotation
-      if (tid == 0) {
-        // only the two entries the next rotation needs, then that rotation;
-        // threads >= 1 write the whole column update (the same values)
-        if (kk + 1 < hi) {
-          const double2 x1 = cadd(cscale(gc, A[(kk + 1) * m + kk]), cmul(cgs, A[(kk + 1) * m + kk + 1]));
-          const double2 y1 = cadd(cscale(gc, A[(kk + 2) * m + kk]), cmul(cgs, A[(kk + 2) * m + kk + 1]));
-          givens(x1, y1, s_gc[kk + 1], s_gs[kk + 1]);
+      if (tid == rt) {
+        for (int row = kk + 1; row <= rmax; ++row) {
+          const double2 a1 = A[row * ld + kk], a2 = A[row * ld + kk + 1];
+          A[row * ld + kk] = cadd(cscale(gc, a1), cmul(cgs, a2));
+          A[row * ld + kk + 1] = cadd(cmul(ngs, a1), cscale(gc, a2));
         }
-      } else {
-        for (int row = l + tid - 1; row <= rmax; row += bd - 1) {
-          const double2 a1 = A[row * m + kk], a2 = A[row * m + kk + 1];
-          A[row * m + kk] = cadd(cscale(gc, a1), cmul(cgs, a2));
-          A[row * m + kk + 1] = cadd(cmul(ngs, a1), cscale(gc, a2));
+        if (kk + 1 < hi) givens(A[(kk + 1) * ld + kk], A[(kk + 2) * ld + kk], s_gc[kk + 1], s_gs[kk + 1]);
+      } else if (tid < nwk) {
+        for (int row = l + tid; row <= kk; row += nwk) {
+          const double2 a1 = A[row * ld + kk], a2 = A[row * ld + kk + 1];
+          A[row * ld + kk] = cadd(cscale(gc, a1), cmul(cgs, a2));
+          A[row * ld + kk + 1] = cadd(cmul(ngs, a1), cscale(gc, a2));
         }
       }
     }
     __syncthreads();
+    if (tid == 0) {
+      const long long t1 = clock64();
+      t_rot += t1 - t0;
+      t0 = t1;
+    }
     // deferred: rows above the block (column rotations), columns right of it
     // (row rotations), and the Schur vectors (column rotations)
     for (int t = tid; t < l + (m - 1 - hi) + m; t += bd) {
@@ -460,26 +474,30 @@ __device__ int schur_block(double2 *A, double2 *Z, int m, double2 *u, long long 
         for (int kk = l; kk < hi; ++kk) {
           const double gc = s_gc[kk];
           const double2 gs = s_gs[kk];
-          const double2 a1 = X[row * m + kk], a2 = X[row * m + kk + 1];
-          X[row * m + kk] = cadd(cscale(gc, a1), cmul(cconj(gs), a2));
-          X[row * m + kk + 1] = cadd(cmul(cneg(gs), a1), cscale(gc, a2));
+          const double2 a1 = X[row * ld + kk], a2 = X[row * ld + kk + 1];
+          X[row * ld + kk] = cadd(cscale(gc, a1), cmul(cconj(gs), a2));
+          X[row * ld + kk + 1] = cadd(cmul(cneg(gs), a1), cscale(gc, a2));
         }
       } else {
         const int col = hi + 1 + (t - l);
         for (int kk = l; kk < hi; ++kk) {
           const double gc = s_gc[kk];
           const double2 gs = s_gs[kk];
-          const double2 a1 = A[kk * m + col], a2 = A[(kk + 1) * m + col];
-          A[kk * m + col] = cadd(cscale(gc, a1), cmul(gs, a2));
-          A[(kk + 1) * m + col] = cadd(cmul(cneg(cconj(gs)), a1), cscale(gc, a2));
+          const double2 a1 = A[kk * ld + col], a2 = A[(kk + 1) * ld + col];
+          A[kk * ld + col] = cadd(cscale(gc, a1), cmul(gs, a2));
+          A[(kk + 1) * ld + col] = cadd(cmul(cneg(cconj(gs)), a1), cscale(gc, a2));
         }
       }
     }
     __syncthreads();
+    if (tid == 0) t_def += clock64() - t0;
   }
   if (clk != nullptr && tid == 0) {
     clk[8] = total;
     clk[9] = rotations;
+    clk[10] = t_scan;
+    clk[11] = t_rot;
+    clk[12] = t_def;
   }
   return 0;
 }
@@ -510,26 +528,29 @@ __global__ void __launch_bounds__(CE_THREADS) gmresdr_cycle_end_kernel(CycleEndA
     if (tid == 0) a.ck[0] = make_double2(res, 0.0);
     return;
   }
-  double2 *A = sm;               // m x m
-  double2 *Z = A + m * m;        // m x m
-  double2 *v1 = Z + m * m;       // m+1
+  // leading dimension = 1 mod 8 complex numbers: row-strided (column) access
+  // by consecutive threads then walks all shared-memory banks
+  const int ld = cyc_ld(m);
+  double2 *A = sm;               // m x ld
+  double2 *Z = A + m * ld;       // m x ld
+  double2 *v1 = Z + m * ld;      // m+1
   double2 *v2 = v1 + (m + 1);    // m+1
   // harmonic Ritz matrix H_m + |h_{m+1,m}|^2 f e_m^T with H_m^dagger f = e_m
   for (int e = tid; e < m * m; e += bd) {
     const int i = e / m, j = e % m;
-    A[e] = a.H[i * m + j];
-    Z[j * m + i] = cconj(a.H[i * m + j]);
+    A[i * ld + j] = a.H[i * m + j];
+    Z[j * ld + i] = cconj(a.H[i * m + j]);
   }
   for (int i = tid; i < m; i += bd) v1[i] = make_double2(i == m - 1 ? 1.0 : 0.0, 0.0);
   __syncthreads();
-  lu_factor_block(Z, m, m, piv);
+  lu_factor_block(Z, ld, m, piv);
   __syncthreads();
-  lu_solve_block(Z, m, piv, m, v1, 1, 1);
+  lu_solve_block(Z, ld, piv, m, v1, 1, 1);
   STAMP(2)
   const double hh = cnorm2(a.H[m * m + m - 1]);
-  for (int i = tid; i < m; i += bd) A[i * m + m - 1] = cadd(A[i * m + m - 1], cscale(hh, v1[i]));
+  for (int i = tid; i < m; i += bd) A[i * ld + m - 1] = cadd(A[i * ld + m - 1], cscale(hh, v1[i]));
   __syncthreads();
-  if (schur_block(A, Z, m, v2, a.clk)) {
+  if (schur_block(A, Z, m, ld, v2, a.clk)) {
     if (tid == 0) a.flags[0] = 1;
     return;
   }
@@ -537,11 +558,11 @@ __global__ void __launch_bounds__(CE_THREADS) gmresdr_cycle_end_kernel(CycleEndA
   STAMP(3)
   // order eigenvalues by (|theta|, Re, Im), index as the final tie-break
   for (int i = tid; i < m; i += bd) {
-    const double2 ti = A[i * m + i];
+    const double2 ti = A[i * ld + i];
     const double ai = cabs_(ti);
     int rank = 0;
     for (int j = 0; j < m; ++j) {
-      const double2 tj = A[j * m + j];
+      const double2 tj = A[j * ld + j];
       const double aj = cabs_(tj);
       const bool less = aj < ai || (aj == ai && (tj.x < ti.x || (tj.x == ti.x && (tj.y < ti.y ||
                                                    (tj.y == ti.y && j < i)))));
@@ -555,12 +576,12 @@ __global__ void __launch_bounds__(CE_THREADS) gmresdr_cycle_end_kernel(CycleEndA
   double2 *G = a.work;
   for (int q = wid; q < k; q += nw) {
     const int i = sel[q];
-    const double2 lam = A[i * m + i];
+    const double2 lam = A[i * ld + i];
     double2 rhs[3], y[3];  // rows lane, lane+32, lane+64
 #pragma unroll
     for (int t = 0; t < 3; ++t) {
       const int row = lane + 32 * t;
-      rhs[t] = row < i ? cneg(A[row * m + i]) : make_double2(0.0, 0.0);
+      rhs[t] = row < i ? cneg(A[row * ld + i]) : make_double2(0.0, 0.0);
       y[t] = row == i ? make_double2(1.0, 0.0) : make_double2(0.0, 0.0);
     }
     const double smin = fmax(2.220446049250313e-16 * (cabs1(lam) + 1e-300), 1e-290);
@@ -568,7 +589,7 @@ __global__ void __launch_bounds__(CE_THREADS) gmresdr_cycle_end_kernel(CycleEndA
       const int own = j & 31, slot = j >> 5;
       double2 yj = make_double2(0.0, 0.0);
       if (lane == own) {
-        double2 den = csub(A[j * m + j], lam);
+        double2 den = csub(A[j * ld + j], lam);
         if (cabs1(den) < smin) den = make_double2(smin, 0.0);
         const double2 r = slot == 0 ? rhs[0] : (slot == 1 ? rhs[1] : rhs[2]);
         yj = cdiv(r, den);
@@ -581,7 +602,7 @@ __global__ void __launch_bounds__(CE_THREADS) gmresdr_cycle_end_kernel(CycleEndA
 #pragma unroll
       for (int t = 0; t < 3; ++t) {
         const int row = lane + 32 * t;
-        if (row < j) rhs[t] = csub(rhs[t], cmul(A[row * m + j], yj));
+        if (row < j) rhs[t] = csub(rhs[t], cmul(A[row * ld + j], yj));
       }
     }
     // g = Z y
@@ -594,7 +615,7 @@ __global__ void __launch_bounds__(CE_THREADS) gmresdr_cycle_end_kernel(CycleEndA
         double2 yj = slot == 0 ? y[0] : (slot == 1 ? y[1] : y[2]);
         yj.x = __shfl_sync(0xffffffffu, yj.x, own);
         yj.y = __shfl_sync(0xffffffffu, yj.y, own);
-        if (row < m) g = cfma(Z[row * m + j], yj, g);
+        if (row < m) g = cfma(Z[row * ld + j], yj, g);
       }
       if (row < m) G[row * k + q] = g;
     }
@@ -650,15 +671,15 @@ __global__ void __launch_bounds__(CE_THREADS) gmresdr_cycle_end_kernel(CycleEndA
     for (int i = 0; i <= m; ++i) s = cfmac(P[i * ldp + r], a.rho[i], s);
     a.ck[r] = s;
   }
-  for (int q = tid; q < k; q += bd) a.theta[q] = A[sel[q] * m + sel[q]];
+  for (int q = tid; q < k; q += bd) a.theta[q] = A[sel[q] * ld + sel[q]];
   __syncthreads();
   STAMP(6)
 #undef STAMP
 }
 
 size_t gmresdr_cycle_end_smem(int m) {
-  const size_t lsq = (size_t)(m + 1) * m + 3 * (m + 1);
-  const size_t eig = (size_t)2 * m * m + 2 * (m + 1);
+  const size_t lsq = (size_t)(m + 1) * cyc_ld(m) + 3 * (m + 1);
+  const size_t eig = (size_t)2 * m * cyc_ld(m) + 2 * (m + 1);
   return (lsq > eig ? lsq : eig) * sizeof(double2);
 }
 

@@ -230,7 +230,7 @@ int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, doubl
   double2 *work = ar.take<double2>((size_t)2 * (m + 1) * (m + 1));
   // WD_TRACE_DENSE=1 prints the SM-clock split of every cycle-end kernel
   const bool trace_dense = std::getenv("WD_TRACE_DENSE") != nullptr;
-  long long *clk = trace_dense ? ar.take<long long>(10) : nullptr;
+  long long *clk = trace_dense ? ar.take<long long>(13) : nullptr;
   if (ar.failed) return WD_OUT_OF_MEMORY;
 
   long long mvp = 0, mvp_extra = 0;
@@ -296,14 +296,15 @@ int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, doubl
     a.clk = clk;
     RET_IF(launch_ok(launch_gmresdr_cycle_end(a, s), "cycle_end"));
     if (clk) {
-      long long hc[10] = {0};
+      long long hc[13] = {0};
       WD_CK(cudaMemcpyAsync(hc, clk, sizeof(hc), cudaMemcpyDeviceToHost, s));
       WD_CK(cudaStreamSynchronize(s));
       std::fprintf(stderr,
                    "cycle_end clk: lsq %lld lu %lld hessenberg %lld qr-iter %lld eigvec %lld "
-                   "qr(P) %lld products %lld | sweeps %lld rotations %lld\n",
+                   "qr(P) %lld products %lld | sweeps %lld rotations %lld scan %lld rot %lld "
+                   "deferred %lld\n",
                    hc[1] - hc[0], hc[2] - hc[1], hc[7] - hc[2], hc[3] - hc[7], hc[4] - hc[3],
-                   hc[5] - hc[4], hc[6] - hc[5], hc[8], hc[9]);
+                   hc[5] - hc[4], hc[6] - hc[5], hc[8], hc[9], hc[10], hc[11], hc[12]);
     }
     int hflags[2], hme;
     double hres;
