@@ -76,6 +76,7 @@ SIGNATURES = {
     "tm_multishift_solve": (I, [P, P, P, I, ctypes.POINTER(D), I, D, I, I, I, ctypes.POINTER(WdStats), P]),
     "dbicgstab_solve_mixed": (I, [P, P, P, P, I, D, I, I, ctypes.POINTER(WdStats), P]),
     "wd_apply_f32": (I, [P, P, P, I, I, P]),
+    "wd_apply_f32_noalloc": (I, [P, P, P, I, I, P]),
     "wd_profile_enable": (I, [P, ctypes.c_uint]),
     "wd_profile_read": (I, [P, ctypes.POINTER(WdProfile)]),
     "wd_destroy": (None, [P]),
