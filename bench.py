@@ -45,6 +45,10 @@ SM_MAX_MHZ = 2070.0
 
 DSLASH_FLOPS_PER_SITE = 1368      # 1320 hopping + 48 for 1 - kappa*D
 DSLASH_BYTES_PER_SITE = 960       # 192 in + 192 out + 4 links x 144 (FP64)
+# DRAM bytes (read + write) per site update of wilson_f64_kernel from one ncu
+# capture of a 10-system launch at 16^4 (497.6 MB / 655,360 site updates);
+# the bench scales it to a launch by the site updates the launch processed.
+DSLASH_DRAM_BYTES_PER_SITE_UPDATE = 497.6e6 / 655360
 METRIC = "D-BiCGStab solves/s at rel. residual 1e-10; dslash GB/s vs HBM roofline"
 
 
@@ -85,6 +89,17 @@ def rank_sources(cfg, rank, count):
         else:
             out.append(L.gaussian_spinor(cfg.dims, seed))
     return np.stack(out)
+
+
+def max_over_ranks(value: float, device="cpu") -> float:
+    """The largest `value` over all ranks (the step time of the slowest GPU);
+    the identity on one process."""
+    import torch
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
 
 
 # ------------------------------------------------------------------ clocks
@@ -255,7 +270,7 @@ def gpu_arm(args, cfg, rank, world, local_rank):
         defl.close()
         if rc != 0 or rc2 != 0 or not all(s["converged"] for s in sts):
             raise RuntimeError(f"solve did not converge: gmresdr rc={rc}, dbicgstab rc={rc2}")
-        return st, sts
+        return st, sts, theta
 
     for _ in range(args.warmup):
         step(b0, x0, B, X)
@@ -284,11 +299,7 @@ def gpu_arm(args, cfg, rank, world, local_rank):
     prof_live = op.profile_read()
     op.profile(mask=0)
     clk = clocks.stop()
-    total_ms = sum(ms_steps)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(ms_steps), dev)
 
     # ---- one more step with every kernel category timed: the breakdown
     op.profile(mask=0xF)
@@ -302,7 +313,9 @@ def gpu_arm(args, cfg, rank, world, local_rank):
         rc, st0, _, _ = op.gmresdr(b0, x0.zero_(), cfg.m, cfg.k, cfg.tol, 400000, V_out=V)
         defl = op.deflation(V, cfg.k)
         res = {}
-        for name, fn in (("fp64", op.dbicgstab), ("mixed", op.dbicgstab_mixed)):
+        for name, fn, bits in (("fp64", op.dbicgstab, 32), ("mixed", op.dbicgstab_mixed, 32),
+                               ("mixed16", op.dbicgstab_mixed, 16)):
+            op.set_mixed_storage(bits)
             X.zero_()
             fn(B, X, defl, tol=cfg.tol)            # warm
             ts = []
@@ -319,6 +332,7 @@ def gpu_arm(args, cfg, rank, world, local_rank):
                     raise RuntimeError(f"{name} D-BiCGStab did not converge")
             res[name] = (min(ts), ss)
         defl.close()
+        op.set_mixed_storage(32)
         mixed = {
             "what": "D-BiCGStab(k) on the step's sources with the step's V, projection included",
             "fp64_solves_per_s": round(cfg.n_rhs / (res["fp64"][0] * 1e-3), 3),
@@ -327,15 +341,24 @@ def gpu_arm(args, cfg, rank, world, local_rank):
             "fp64_iters": [q["iters"] for q in res["fp64"][1]],
             "mixed_iters": [q["iters"] for q in res["mixed"][1]],
             "mixed_max_true_rel_res": max(q["true_rel_res"] for q in res["mixed"][1]),
+            "mixed16_solves_per_s": round(cfg.n_rhs / (res["mixed16"][0] * 1e-3), 3),
+            "speedup16": round(res["fp64"][0] / res["mixed16"][0], 3),
+            "mixed16_iters": [q["iters"] for q in res["mixed16"][1]],
+            "mixed16_max_true_rel_res": max(q["true_rel_res"] for q in res["mixed16"][1]),
+            "storage": {"mixed": "FP32 vectors and links", "mixed16": "FP16 p, v, t and links "
+                        "(per-site norm), FP32 r, r_hat, x increment"},
             "reliable_every": 50,
         }
 
-    gst, sts = last
+    gst, sts, theta = last
+    th = np.sort(np.abs(np.asarray(theta)))
     counts = {"gmresdr_mvp": gst["mvp"], "gmresdr_cycles": gst["cycles"],
               "dbicgstab_mvp": [s["mvp"] for s in sts],
               "dbicgstab_iters": [s["iters"] for s in sts],
               "true_rel_res_max": max(s["true_rel_res"] for s in sts),
-              "gmresdr_true_rel_res": gst["true_rel_res"]}
+              "gmresdr_true_rel_res": gst["true_rel_res"],
+              "harmonic_ritz_abs": {"min": float(th[0]), "median": float(th[len(th) // 2]),
+                                    "max": float(th[-1])}}
 
     # ---- e2e: the same step through the C ABI with host buffers
     e2e = None
@@ -356,11 +379,7 @@ def gpu_arm(args, cfg, rank, world, local_rank):
             step(b0h, x0h, Bh, Xh)
             torch.cuda.synchronize()
             wall.append(time.perf_counter() - t)
-        tot = sum(wall)
-        if world > 1:
-            tt = torch.tensor([tot], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            tot = float(tt.item())
+        tot = max_over_ranks(sum(wall), dev)
         h2d = (2 + 2 * cfg.n_rhs) * n * 16      # b0, x0, B, X0 staged in
         d2h = (1 + cfg.n_rhs) * n * 16          # x and X copied back
         e2e = {"value": cfg.n_rhs * args.steps * world / tot, "unit": "solves/s",
@@ -390,7 +409,10 @@ def roofline(res, peaks, fp64_peak):
         "unit": "TFLOP/s",
         "frac": round(tflops / fp64_peak["tflops"], 4),
         "peak_source": fp64_peak["source"],
-        "traffic": None,
+        "traffic": round(DSLASH_DRAM_BYTES_PER_SITE_UPDATE * sites_per_launch),
+        "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 16^4 "
+                          "10-system launch (759 B per site update), scaled to the average "
+                          "launch by site updates",
         "algorithmic_flops_per_launch": flops,
         "avg_launch_ms": avg_ms,
         "launches": launches,

@@ -224,6 +224,41 @@ int dbicgstab_solve_mixed(wd_handle h, wd_deflation d, const void *B, void *X,
 int wd_apply_f32(wd_handle h, const void *in, void *out, int nrhs, int dagger,
                  wd_stream stream);
 
+/* Autotuner of the FP32 Wilson kernel (not in the paper): times every launch
+ * shape (R = 1, 2, 4 right-hand sides per thread, 64/128/256 threads per
+ * block) for nrhs right-hand sides on this lattice and keeps the fastest in
+ * the handle (nrhs >= 33 share one slot).  The mixed solver runs it on
+ * first use of an nrhs; R, threads, ms (NULL or host) report the choice.
+ * wd_set_f32_shape fixes a shape by hand (R = threads = 0: back to the
+ * default R by nrhs, 128 threads). */
+int wd_autotune_f32(wd_handle h, int nrhs, int *R, int *threads, float *ms,
+                    wd_stream stream);
+int wd_set_f32_shape(wd_handle h, int nrhs, int R, int threads);
+
+/* Storage of the mixed solver's iteration (not in the paper): bits = 32
+ * (default) keeps every Krylov vector in FP32; bits = 16 stores the links
+ * and the three vectors the operator reads or writes (p, v, t) in FP16,
+ * each site's 12 complex numbers scaled by that site's largest component
+ * (one FP32 norm per site), while r, r_hat and the solution increment stay
+ * FP32.  Arithmetic is FP32 either way and the reliable updates and the
+ * convergence test are FP64, so the tolerance means the same; FP16 storage
+ * halves the bytes of the operator and may take more iterations.  Applies
+ * to dbicgstab_solve_mixed and to tm_multishift_solve with mixed = 1.
+ * Returns WD_BAD_ARG for any other bits. */
+int wd_set_mixed_storage(wd_handle h, int bits);
+
+/* out = A in computed by the FP16-storage kernel: in and out are FP64 device
+ * vectors in the boundary layout, rounded to the half format on entry
+ * (per-site norm, see above) and widened on exit; FP32 arithmetic. */
+int wd_apply_f16(wd_handle h, const void *in, void *out, int nrhs, int dagger,
+                 wd_stream stream);
+
+/* Autotuner and fixed shapes of the FP16-storage Wilson kernel, as
+ * wd_autotune_f32 / wd_set_f32_shape (separate slots per handle). */
+int wd_autotune_f16(wd_handle h, int nrhs, int *R, int *threads, float *ms,
+                    wd_stream stream);
+int wd_set_f16_shape(wd_handle h, int nrhs, int R, int threads);
+
 /* ---------------------------------------------------------- no allocation */
 
 /* The paper has no counterpart to this entry point: it is a service for

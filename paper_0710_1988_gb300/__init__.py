@@ -217,12 +217,45 @@ class WilsonOperator:
         out = [s.as_dict() for s in sts]
         return rc, [out[i * nrhs:(i + 1) * nrhs] for i in range(ns)]
 
+    def autotune_f32(self, nrhs: int, stream=None):
+        """Time every FP32 launch shape for nrhs right-hand sides; returns
+        (R, threads per block, ms) of the fastest, now used by this handle."""
+        R, T, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        check(lib().wd_autotune_f32(self._h, int(nrhs), ctypes.byref(R), ctypes.byref(T),
+                                    ctypes.byref(ms), _stream(stream)))
+        return R.value, T.value, ms.value
+
+    def set_f32_shape(self, nrhs: int, R: int, threads: int):
+        check(lib().wd_set_f32_shape(self._h, int(nrhs), int(R), int(threads)))
+
     def apply_f32(self, x, out, dagger: bool = False, stream=None):
         """out = A x with the FP32 kernel (FP64 vectors rounded on entry)."""
         nrhs = self._nrhs(x)
         check(lib().wd_apply_f32(self._h, _ptr(x), _ptr(out), nrhs, 1 if dagger else 0,
                                  _stream(stream, x, out)))
         return out
+
+    def apply_f16(self, x, out, dagger: bool = False, stream=None):
+        """out = A x with the FP16-storage kernel (FP64 vectors rounded to
+        half with a per-site norm on entry, FP32 arithmetic)."""
+        nrhs = self._nrhs(x)
+        check(lib().wd_apply_f16(self._h, _ptr(x), _ptr(out), nrhs, 1 if dagger else 0,
+                                 _stream(stream, x, out)))
+        return out
+
+    def autotune_f16(self, nrhs: int, stream=None):
+        """As autotune_f32, for the FP16-storage kernel."""
+        R, T, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        check(lib().wd_autotune_f16(self._h, int(nrhs), ctypes.byref(R), ctypes.byref(T),
+                                    ctypes.byref(ms), _stream(stream)))
+        return R.value, T.value, ms.value
+
+    def set_f16_shape(self, nrhs: int, R: int, threads: int):
+        check(lib().wd_set_f16_shape(self._h, int(nrhs), int(R), int(threads)))
+
+    def set_mixed_storage(self, bits: int):
+        """Storage of the mixed solver's Krylov vectors: 32 (default) or 16."""
+        check(lib().wd_set_mixed_storage(self._h, int(bits)))
 
     def dbicgstab_oneshot(self, B, X, V=None, k: int = 0, U=None, tol: float = 1e-10,
                           max_iter: int = 100000, stream=None):

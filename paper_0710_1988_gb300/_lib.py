@@ -77,6 +77,12 @@ SIGNATURES = {
     "dbicgstab_solve_mixed": (I, [P, P, P, P, I, D, I, I, ctypes.POINTER(WdStats), P]),
     "wd_apply_f32": (I, [P, P, P, I, I, P]),
     "wd_apply_f32_noalloc": (I, [P, P, P, I, I, P]),
+    "wd_autotune_f32": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float), P]),
+    "wd_set_f32_shape": (I, [P, I, I, I]),
+    "wd_set_mixed_storage": (I, [P, I]),
+    "wd_apply_f16": (I, [P, P, P, I, I, P]),
+    "wd_autotune_f16": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float), P]),
+    "wd_set_f16_shape": (I, [P, I, I, I]),
     "wd_profile_enable": (I, [P, ctypes.c_uint]),
     "wd_profile_read": (I, [P, ctypes.POINTER(WdProfile)]),
     "wd_destroy": (None, [P]),

@@ -132,9 +132,17 @@ extern "C" int wd_create(const int lat[4], const void *links, double kappa, doub
   wd_context *h = new wd_context();
   h->prof.d_sites = nullptr;
   h->links32 = nullptr;
+  h->links16 = nullptr;
+  h->mixed_bits = 32;
   h->side = nullptr;
   h->ev_in = h->ev_out = nullptr;
   h->eo = 0;
+  for (int i = 0; i < WD_TUNE_SLOTS; ++i) {
+    h->tune_R[i] = h->tune_T[i] = 0;
+    h->tune_ms[i] = 0.f;
+    h->tune16_R[i] = h->tune16_T[i] = 0;
+    h->tune16_ms[i] = 0.f;
+  }
   h->eo_tmp = nullptr;
   h->eo_tmp_cap = 0;
   for (int i = 0; i < 4; ++i) h->dims[i] = lat[i];
@@ -235,6 +243,7 @@ extern "C" void wd_destroy(wd_handle h) {
   cudaDeviceSynchronize();
   h->prof.destroy();
   if (h->links32) cudaFree(h->links32);
+  if (h->links16) cudaFree(h->links16);
   if (h->eo_tmp) cudaFree(h->eo_tmp);
   if (h->side) cudaStreamDestroy(h->side);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
@@ -702,6 +711,122 @@ extern "C" int wd_apply_f32(wd_handle h, const void *in, void *out, int nrhs, in
   if (e == cudaSuccess) e = launch_f32_to_f64(b, static_cast<double2 *>(out), h->V, nrhs, s);
   ar.release();
   if (e != cudaSuccess) return cuda_fail(e, "wd_apply_f32");
+  return WD_OK;
+}
+
+extern "C" int wd_apply_f16(wd_handle h, const void *in, void *out, int nrhs, int dagger,
+                            wd_stream stream) {
+  ProfScope prof_scope_(h ? &h->prof : nullptr);
+  if (h == nullptr) return bad("wd_apply_f16: NULL handle");
+  if (h->eo) return bad("wd_apply_f16: the FP16 kernel acts on the full operator");
+  if (in == nullptr || out == nullptr) return bad("wd_apply_f16: NULL vector");
+  if (nrhs < 1 || nrhs > 65535) return bad("wd_apply_f16: nrhs must be in [1, 65535]");
+  if (!is_device_pointer(in) || !is_device_pointer(out))
+    return bad("wd_apply_f16: in and out must be device pointers");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = ensure_links16(h, s);
+  if (rc != WD_OK) return rc;
+  Arena ar;
+  ar.pool = h->pool;
+  ar.stream = s;
+  const size_t nv = (size_t)nrhs * h->V;
+  Half16 a{ar.take<uint4>(3 * nv), ar.take<float>(nv)};
+  Half16 b{ar.take<uint4>(3 * nv), ar.take<float>(nv)};
+  if (ar.failed) return bad_alloc();
+  cudaError_t e = launch_f64_to_f16(static_cast<const double2 *>(in), a, h->V, nrhs, s);
+  if (e == cudaSuccess)
+    e = launch_wilson_f16(h, h->links16, a, nullptr, b, nrhs, dagger ? 1 : 0, EPI_NONE, nullptr,
+                          nullptr, nullptr, nullptr, M_ALL, s);
+  if (e == cudaSuccess) e = launch_f16_to_f64(b, static_cast<double2 *>(out), h->V, nrhs, s);
+  ar.release();
+  if (e != cudaSuccess) return cuda_fail(e, "wd_apply_f16");
+  return WD_OK;
+}
+
+extern "C" int wd_autotune_f16(wd_handle h, int nrhs, int *R, int *threads, float *ms,
+                               wd_stream stream) {
+  if (h == nullptr) return bad("wd_autotune_f16: NULL handle");
+  if (h->eo) return bad("wd_autotune_f16: the FP16 kernel acts on the full operator");
+  if (nrhs < 1 || nrhs > 65535) return bad("wd_autotune_f16: nrhs must be in [1, 65535]");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = ensure_links16(h, s);
+  if (rc != WD_OK) return rc;
+  Arena ar;
+  ar.pool = h->pool;
+  ar.stream = s;
+  const size_t nv = (size_t)nrhs * h->V;
+  Half16 a{ar.take<uint4>(3 * nv), ar.take<float>(nv)};
+  Half16 b{ar.take<uint4>(3 * nv), ar.take<float>(nv)};
+  if (ar.failed) return bad_alloc();
+  cudaError_t e = cudaMemsetAsync(a.v, 0, sizeof(uint4) * 3 * nv, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.n, 0, sizeof(float) * nv, s);
+  if (e == cudaSuccess) e = tune_wilson_f16(h, h->links16, nrhs, a, b, s);
+  ar.release();
+  if (e != cudaSuccess) return cuda_fail(e, "wd_autotune_f16");
+  const int key = nrhs < WD_TUNE_SLOTS ? nrhs : WD_TUNE_SLOTS - 1;
+  if (R) *R = h->tune16_R[key];
+  if (threads) *threads = h->tune16_T[key];
+  if (ms) *ms = h->tune16_ms[key];
+  return WD_OK;
+}
+
+extern "C" int wd_set_f16_shape(wd_handle h, int nrhs, int R, int threads) {
+  if (h == nullptr) return bad("wd_set_f16_shape: NULL handle");
+  if (nrhs < 1) return bad("wd_set_f16_shape: nrhs must be >= 1");
+  if (!((R == 0 && threads == 0) || ((R == 1 || R == 2 || R == 4) &&
+                                     (threads == 64 || threads == 128 || threads == 256))))
+    return bad("wd_set_f16_shape: R in {1, 2, 4} and threads in {64, 128, 256} (or both 0)");
+  const int key = nrhs < WD_TUNE_SLOTS ? nrhs : WD_TUNE_SLOTS - 1;
+  h->tune16_R[key] = R;
+  h->tune16_T[key] = threads;
+  h->tune16_ms[key] = 0.f;
+  return WD_OK;
+}
+
+extern "C" int wd_set_mixed_storage(wd_handle h, int bits) {
+  if (h == nullptr) return bad("wd_set_mixed_storage: NULL handle");
+  if (bits != 32 && bits != 16) return bad("wd_set_mixed_storage: bits must be 32 or 16");
+  h->mixed_bits = bits;
+  return WD_OK;
+}
+
+// ------------------------------------------------------------------ autotuner
+
+extern "C" int wd_autotune_f32(wd_handle h, int nrhs, int *R, int *threads, float *ms,
+                               wd_stream stream) {
+  if (h == nullptr) return bad("wd_autotune_f32: NULL handle");
+  if (h->eo) return bad("wd_autotune_f32: the FP32 kernel acts on the full operator");
+  if (nrhs < 1 || nrhs > 65535) return bad("wd_autotune_f32: nrhs must be in [1, 65535]");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = ensure_links32(h, s);
+  if (rc != WD_OK) return rc;
+  Arena ar;
+  ar.pool = h->pool;
+  ar.stream = s;
+  const size_t v32 = (size_t)nrhs * 6 * h->V;
+  float4 *a = ar.take<float4>(v32), *b = ar.take<float4>(v32);
+  if (ar.failed) return bad_alloc();
+  cudaError_t e = cudaMemsetAsync(a, 0, sizeof(float4) * v32, s);
+  if (e == cudaSuccess) e = tune_wilson_f32(h, h->links32, nrhs, a, b, s);
+  ar.release();
+  if (e != cudaSuccess) return cuda_fail(e, "wd_autotune_f32");
+  const int key = nrhs < WD_TUNE_SLOTS ? nrhs : WD_TUNE_SLOTS - 1;
+  if (R) *R = h->tune_R[key];
+  if (threads) *threads = h->tune_T[key];
+  if (ms) *ms = h->tune_ms[key];
+  return WD_OK;
+}
+
+extern "C" int wd_set_f32_shape(wd_handle h, int nrhs, int R, int threads) {
+  if (h == nullptr) return bad("wd_set_f32_shape: NULL handle");
+  if (nrhs < 1) return bad("wd_set_f32_shape: nrhs must be >= 1");
+  if (!((R == 0 && threads == 0) || ((R == 1 || R == 2 || R == 4) &&
+                                     (threads == 64 || threads == 128 || threads == 256))))
+    return bad("wd_set_f32_shape: R in {1, 2, 4} and threads in {64, 128, 256} (or both 0)");
+  const int key = nrhs < WD_TUNE_SLOTS ? nrhs : WD_TUNE_SLOTS - 1;
+  h->tune_R[key] = R;
+  h->tune_T[key] = threads;
+  h->tune_ms[key] = 0.f;
   return WD_OK;
 }
 

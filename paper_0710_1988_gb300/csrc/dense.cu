@@ -382,20 +382,30 @@ __device__ int schur_block(double2 *A, double2 *Z, int m, int ld, double2 *u, lo
   // the sweep's rotations afterwards, one thread per row or column.
   __shared__ double s_gc[CE_MAXM];
   __shared__ double2 s_gs[CE_MAXM];
+  __shared__ int s_l[2];    // deflation point of the scan, double-buffered
   const int rt = bd - 32;   // rotation thread
   const int nwk = bd - 32;  // threads of the bulk updates
   long long rotations = 0, t_scan = 0, t_rot = 0, t_def = 0, t0 = 0;
-  int hi = m - 1, its = 0, total = 0;
+  int hi = m - 1, its = 0, total = 0, scan = 0;
+  if (tid < 2) s_l[tid] = 0;
+  __syncthreads();
   while (hi > 0) {
     if (total >= 30 * m) return 1;
     if (tid == 0) t0 = clock64();
-    int l = hi;
-    for (; l > 0; --l) {
-      double tst = cabs1(A[(l - 1) * ld + l - 1]) + cabs1(A[l * ld + l]);
+    // l = the largest index in [1, hi] whose subdiagonal entry is negligible
+    // (0 if none): one candidate per thread, the maximum by a shared atomic.
+    // The slot written now was last read before the previous scan's barrier
+    // and is reset for the scan after next.
+    const int slot = scan & 1;
+    for (int q = 1 + tid; q <= hi; q += bd) {
+      double tst = cabs1(A[(q - 1) * ld + q - 1]) + cabs1(A[q * ld + q]);
       if (tst == 0.0) tst = anorm;
-      if (cabs1(A[l * ld + l - 1]) <= 2.220446049250313e-16 * tst) break;
+      if (cabs1(A[q * ld + q - 1]) <= 2.220446049250313e-16 * tst) atomicMax(&s_l[slot], q);
     }
     __syncthreads();
+    const int l = s_l[slot];
+    if (tid == 0) s_l[slot ^ 1] = 0;
+    ++scan;
     if (l > 0 && tid == 0) A[l * ld + l - 1] = make_double2(0.0, 0.0);
     __syncthreads();
     if (l == hi) {

@@ -125,8 +125,8 @@ __device__ __forceinline__ void hop32(const float4 *__restrict__ links, const fl
 
 // EPI_NONE: out = A in.   EPI_DOT: out = A in, partial <aux, out>, ||out||^2.
 // EPI_TSTT (FUSED): out = A s with s = in - alpha in2, partial <out, s>, ||out||^2.
-template <int R, bool DAG, int EPI, bool FUSED>
-__global__ void __launch_bounds__(128)
+template <int R, int TPB, bool DAG, int EPI, bool FUSED>
+__global__ void __launch_bounds__(TPB)
 wilson_f32_kernel(const float4 *__restrict__ links, const float4 *__restrict__ in,
                   const float4 *__restrict__ in2, float4 *__restrict__ out, LatticeGeom g,
                   float kappa, float mu, int nrhs, const BicgScalars *__restrict__ sc,
@@ -210,7 +210,8 @@ wilson_f32_kernel(const float4 *__restrict__ links, const float4 *__restrict__ i
     }
   }
   if (EPI != EPI_NONE) {
-    __shared__ double sh[R][3][4];  // 128 threads = 4 warps
+    constexpr int NW = TPB / 32;
+    __shared__ double sh[R][3][NW];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int r = 0; r < R; ++r)
@@ -225,47 +226,126 @@ wilson_f32_kernel(const float4 *__restrict__ links, const float4 *__restrict__ i
     if (threadIdx.x < R * 3) {
       const int r = threadIdx.x / 3, q = threadIdx.x % 3;
       if (on[r]) {
-        const double t = ((sh[r][q][0] + sh[r][q][1]) + sh[r][q][2]) + sh[r][q][3];
+        double t = 0.0;
+#pragma unroll
+        for (int w2 = 0; w2 < NW; ++w2) t += sh[r][q][w2];
         partial[((long long)(r0 + r) * gridDim.x + blockIdx.x) * 3 + q] = t;
       }
     }
   }
 }
 
-template <int R>
-static cudaError_t launch_w32_r(const Mixed32 &m, const float4 *in, const float4 *in2, float4 *out,
-                                int nrhs, int dagger, int epi, const BicgScalars *sc,
-                                const float4 *aux, double *partial, const int *status,
-                                unsigned mask, cudaStream_t s) {
+template <int R, int TPB>
+static cudaError_t launch_w32(const Mixed32 &m, const float4 *in, const float4 *in2, float4 *out,
+                              int nrhs, int dagger, int epi, const BicgScalars *sc,
+                              const float4 *aux, double *partial, const int *status,
+                              unsigned mask, cudaStream_t s) {
   const wd_context *h = m.h;
   LatticeGeom g = geom_of(h);
-  dim3 grid((unsigned)((h->V + 127) / 128), (nrhs + R - 1) / R);
+  dim3 grid((unsigned)((h->V + TPB - 1) / TPB), (nrhs + R - 1) / R);
   const float kap = (float)h->kappa, mu = (float)h->mu;
   if (epi == EPI_DOT)
-    wilson_f32_kernel<R, false, EPI_DOT, false><<<grid, 128, 0, s>>>(m.links, in, nullptr, out, g, kap, mu, nrhs, sc, aux, partial, status, mask);
+    wilson_f32_kernel<R, TPB, false, EPI_DOT, false><<<grid, TPB, 0, s>>>(m.links, in, nullptr, out, g, kap, mu, nrhs, sc, aux, partial, status, mask);
   else if (epi == EPI_TSTT)
-    wilson_f32_kernel<R, false, EPI_TSTT, true><<<grid, 128, 0, s>>>(m.links, in, in2, out, g, kap, mu, nrhs, sc, aux, partial, status, mask);
+    wilson_f32_kernel<R, TPB, false, EPI_TSTT, true><<<grid, TPB, 0, s>>>(m.links, in, in2, out, g, kap, mu, nrhs, sc, aux, partial, status, mask);
   else if (dagger)
-    wilson_f32_kernel<R, true, EPI_NONE, false><<<grid, 128, 0, s>>>(m.links, in, nullptr, out, g, kap, mu, nrhs, sc, aux, partial, status, mask);
+    wilson_f32_kernel<R, TPB, true, EPI_NONE, false><<<grid, TPB, 0, s>>>(m.links, in, nullptr, out, g, kap, mu, nrhs, sc, aux, partial, status, mask);
   else
-    wilson_f32_kernel<R, false, EPI_NONE, false><<<grid, 128, 0, s>>>(m.links, in, nullptr, out, g, kap, mu, nrhs, sc, aux, partial, status, mask);
+    wilson_f32_kernel<R, TPB, false, EPI_NONE, false><<<grid, TPB, 0, s>>>(m.links, in, nullptr, out, g, kap, mu, nrhs, sc, aux, partial, status, mask);
   return cudaGetLastError();
 }
 
-int wilson32_rhs_per_thread(int nrhs) { return nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1); }
+// Launch shape of the FP32 kernel for nrhs right-hand sides: the autotuned
+// (R, threads per block) of the handle when there is one, else R = 4/2/1 by
+// nrhs and 128 threads.
+void wilson32_shape(const wd_context *h, int nrhs, int *R, int *T) {
+  const int key = nrhs < WD_TUNE_SLOTS ? nrhs : WD_TUNE_SLOTS - 1;
+  if (h->tune_R[key] > 0) {
+    *R = h->tune_R[key];
+    *T = h->tune_T[key];
+    return;
+  }
+  *R = nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1);
+  *T = 128;
+}
+
+cudaError_t launch_wilson_f32_shape(const Mixed32 &m, int R, int T, const float4 *in,
+                                    const float4 *in2, float4 *out, int nrhs, int dagger, int epi,
+                                    const BicgScalars *sc, const float4 *aux, double *partial,
+                                    const int *status, unsigned mask, cudaStream_t s) {
+#define W32(RR, TT) \
+  if (R == RR && T == TT) return launch_w32<RR, TT>(m, in, in2, out, nrhs, dagger, epi, sc, aux, partial, status, mask, s);
+  W32(1, 64) W32(1, 128) W32(1, 256)
+  W32(2, 64) W32(2, 128) W32(2, 256)
+  W32(4, 64) W32(4, 128) W32(4, 256)
+#undef W32
+  return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_wilson_f32(const Mixed32 &m, const float4 *in, const float4 *in2, float4 *out,
                               int nrhs, int dagger, int epi, const BicgScalars *sc,
                               const float4 *aux, double *partial, const int *status,
                               unsigned mask, cudaStream_t s) {
   ProfLaunch prof(PC_DSLASH, s);
-  const int R = wilson32_rhs_per_thread(nrhs);
-  if (R == 4) return launch_w32_r<4>(m, in, in2, out, nrhs, dagger, epi, sc, aux, partial, status, mask, s);
-  if (R == 2) return launch_w32_r<2>(m, in, in2, out, nrhs, dagger, epi, sc, aux, partial, status, mask, s);
-  return launch_w32_r<1>(m, in, in2, out, nrhs, dagger, epi, sc, aux, partial, status, mask, s);
+  int R, T;
+  wilson32_shape(m.h, nrhs, &R, &T);
+  return launch_wilson_f32_shape(m, R, T, in, in2, out, nrhs, dagger, epi, sc, aux, partial, status,
+                                 mask, s);
 }
 
-int wilson32_blocks(const wd_context *h) { return (int)((h->V + 127) / 128); }
+int wilson32_blocks(const wd_context *h, int nrhs) {
+  int R, T;
+  wilson32_shape(h, nrhs, &R, &T);
+  return (int)((h->V + T - 1) / T);
+}
+
+// Autotuner: time every (R, threads per block) on this lattice with nrhs
+// right-hand sides (plain apply, CUDA events, best of 3 after a warm-up)
+// and keep the fastest for the handle.  in and out: scratch FP32 vectors of
+// nrhs * 6 V float4 each.
+cudaError_t tune_wilson_f32(wd_context *h, const float4 *links, int nrhs, const float4 *in,
+                            float4 *out, cudaStream_t s) {
+  const Mixed32 m{h, links};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int bR = 1, bT = 128;
+  const int Rs[3] = {1, 2, 4}, Ts[3] = {64, 128, 256};
+  cudaError_t err = cudaSuccess;
+  for (int R : Rs) {
+    if (R > nrhs && R > 1) continue;
+    for (int T : Ts) {
+      for (int w = 0; w < 2 && err == cudaSuccess; ++w)
+        err = launch_wilson_f32_shape(m, R, T, in, nullptr, out, nrhs, 0, EPI_NONE, nullptr, nullptr,
+                                      nullptr, nullptr, M_ALL, s);
+      float t_best = 1e30f;
+      for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
+        cudaEventRecord(e0, s);
+        err = launch_wilson_f32_shape(m, R, T, in, nullptr, out, nrhs, 0, EPI_NONE, nullptr, nullptr,
+                                      nullptr, nullptr, M_ALL, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        t_best = ms < t_best ? ms : t_best;
+      }
+      if (err == cudaSuccess && t_best < best) {
+        best = t_best;
+        bR = R;
+        bT = T;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return err;
+  const int key = nrhs < WD_TUNE_SLOTS ? nrhs : WD_TUNE_SLOTS - 1;
+  h->tune_R[key] = bR;
+  h->tune_T[key] = bT;
+  h->tune_ms[key] = best;
+  return cudaSuccess;
+}
 
 // ----------------------------------------------------------------- conversions
 

@@ -25,12 +25,14 @@ int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, doubl
                 int max_mv, double2 *V_out, double2 *Hbar_host, double2 *theta_host,
                 wd_stats *stats, cudaStream_t s, double *hist_host, int hist_len, Arena &ar);
 
-// Mixed precision: FP32 Krylov vectors, FP64 reliable updates every
-// reliable_every iterations; R0 = B - A X on entry (FP64).
+// Mixed precision: FP32 Krylov vectors (or, with h->mixed_bits = 16, p, v
+// and t in FP16 storage), FP64 reliable updates every reliable_every
+// iterations; R0 = B - A X on entry (FP64).
 int bicgstab_mixed_batched(wd_context *h, const double2 *B, double2 *X, const double2 *R0,
                            int nrhs, double tol, int max_iter, int reliable_every,
                            wd_stats *stats, cudaStream_t s, Arena &ar);
 int ensure_links32(wd_context *h, cudaStream_t s);
+int ensure_links16(wd_context *h, cudaStream_t s);
 
 // Sec. 4: A(mu_i) X_i = B for i < nshift in the given order, X = [nshift][nrhs][n],
 // each shift projected over the earlier solutions when project != 0.

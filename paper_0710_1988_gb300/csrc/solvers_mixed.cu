@@ -11,6 +11,11 @@
 // system is done only when that FP64 residual is below the tolerance.  Each
 // chunk of iterations between host status reads is captured once as a CUDA
 // graph and replayed.
+//
+// With FP16 storage (h->mixed_bits = 16) the three vectors the operator
+// reads or writes, p, v and t, are half vectors with a per-site norm and the
+// links are FP16; r, r_hat and xs stay FP32 so that the recursive residual
+// and the dots it feeds keep FP32 accuracy between reliable updates.
 #include <cstring>
 #include <vector>
 
@@ -53,16 +58,51 @@ int ensure_links32(wd_context *h, cudaStream_t s) {
   return WD_OK;
 }
 
+int ensure_links16(wd_context *h, cudaStream_t s) {
+  if (h->eo) {
+    set_error("the FP16 kernels act on the full operator: switch the handle back with wd_set_operator(h, 0)");
+    return WD_BAD_ARG;
+  }
+  if (h->links16 != nullptr) return WD_OK;
+  WD_CK(cudaMalloc(&h->links16, sizeof(uint2) * 12 * h->V));
+  WD_CK(launch_links_to_f16(h, h->links16, s));
+  return WD_OK;
+}
+
 int bicgstab_mixed_batched(wd_context *h, const double2 *B, double2 *X, const double2 *R0,
                            int nrhs, double tol, int max_iter, int reliable_every,
                            wd_stats *stats, cudaStream_t s, Arena &ar) {
-  RET_IF(ensure_links32(h, s));
+  const bool half = h->mixed_bits == 16;
+  RET_IF(half ? ensure_links16(h, s) : ensure_links32(h, s));
   const long long V = h->V, n = h->n, n4 = 6 * V;
-  const size_t v32 = (size_t)nrhs * n4;
-  float4 *r = ar.take<float4>(v32), *rhat = ar.take<float4>(v32), *p = ar.take<float4>(v32);
-  float4 *v = ar.take<float4>(v32), *t = ar.take<float4>(v32), *xs = ar.take<float4>(v32);
+  const size_t v32 = (size_t)nrhs * n4, nv = (size_t)nrhs * V;
+  float4 *r = ar.take<float4>(v32), *rhat = ar.take<float4>(v32), *xs = ar.take<float4>(v32);
+  float4 *p = nullptr, *v = nullptr, *t = nullptr;
+  Half16 p16{}, v16{}, t16{};
+  if (half) {
+    p16 = Half16{ar.take<uint4>(3 * nv), ar.take<float>(nv)};
+    v16 = Half16{ar.take<uint4>(3 * nv), ar.take<float>(nv)};
+    t16 = Half16{ar.take<uint4>(3 * nv), ar.take<float>(nv)};
+  } else {
+    p = ar.take<float4>(v32);
+    v = ar.take<float4>(v32);
+    t = ar.take<float4>(v32);
+  }
   double2 *r64 = ar.take<double2>((size_t)nrhs * n), *tmp64 = ar.take<double2>((size_t)nrhs * n);
-  const int nbw = wilson32_blocks(h), nbs = stream32_blocks(n4), nbc = conv_blocks_count(V);
+  {  // pick the Wilson kernel's launch shape for this nrhs once per handle
+    const int key = nrhs < WD_TUNE_SLOTS ? nrhs : WD_TUNE_SLOTS - 1;
+    if (!half && h->tune_R[key] == 0 && !ar.failed) {
+      WD_CK(cudaMemsetAsync(r, 0, sizeof(float4) * v32, s));
+      WD_CK(tune_wilson_f32(h, h->links32, nrhs, r, v, s));
+    }
+    if (half && h->tune16_R[key] == 0 && !ar.failed) {
+      WD_CK(cudaMemsetAsync(p16.v, 0, sizeof(uint4) * 3 * nv, s));
+      WD_CK(cudaMemsetAsync(p16.n, 0, sizeof(float) * nv, s));
+      WD_CK(tune_wilson_f16(h, h->links16, nrhs, p16, v16, s));
+    }
+  }
+  const int nbw = half ? wilson16_blocks(h, nrhs) : wilson32_blocks(h, nrhs);
+  const int nbs = half ? stream16_blocks(V) : stream32_blocks(n4), nbc = conv_blocks_count(V);
   const int nb64 = stream_blocks(n);
   double *part_w = ar.take<double>((size_t)nrhs * nbw * 3);
   double *part_s = ar.take<double>((size_t)nrhs * nbs * 3);
@@ -89,7 +129,10 @@ int bicgstab_mixed_batched(wd_context *h, const double2 *B, double2 *X, const do
   // r32 = r64 for every system, r_hat = r, p = v = 0
   RET_IF(ok(launch_f64_to_f32(r64, r, V, nrhs, nullptr, nullptr, nullptr, M_ALL, s), "to_f32"));
   const unsigned M_LIVE = M_RESTART | M_RECURSIVE;
-  RET_IF(ok(launch_bicg32_restart(rhat, r, p, v, status, M_LIVE, n4, nrhs, s), "restart32"));
+  if (half)
+    RET_IF(ok(launch_bicg16_restart(rhat, r, p16, v16, status, M_LIVE, V, nrhs, s), "restart16"));
+  else
+    RET_IF(ok(launch_bicg32_restart(rhat, r, p, v, status, M_LIVE, n4, nrhs, s), "restart32"));
   // a system whose initial residual already meets tol is checked like any other
   RET_IF(ok(launch_f64_to_f32(r64, r, V, nrhs, rhat, part_c, status, M_RECURSIVE, s), "to_f32"));
   RET_IF(ok(launch_reliable_finalize(part_c, nbc, sc, status, M_RECURSIVE, nrhs, s), "reliable0"));
@@ -98,12 +141,23 @@ int bicgstab_mixed_batched(wd_context *h, const double2 *B, double2 *X, const do
   const int chunk = reliable_every < 10 ? (reliable_every < 1 ? 1 : reliable_every) : 10;
   auto enqueue_chunk = [&]() -> int {
     for (int it = 0; it < chunk; ++it) {
-      RET_IF(ok(launch_bicg32_update_p(p, r, v, sc, status, n4, nrhs, s), "update_p32"));
-      RET_IF(ok(launch_wilson_f32(m, p, nullptr, v, nrhs, 0, EPI_DOT, sc, rhat, part_w, status, M_ACTIVE, s), "w32_dot"));
+      if (half) {
+        RET_IF(ok(launch_bicg16_update_p(p16, r, v16, sc, status, V, nrhs, s), "update_p16"));
+        RET_IF(ok(launch_wilson_f16(h, h->links16, p16, nullptr, v16, nrhs, 0, EPI_DOT, sc, rhat, part_w, status, M_ACTIVE, s), "w16_dot"));
+      } else {
+        RET_IF(ok(launch_bicg32_update_p(p, r, v, sc, status, n4, nrhs, s), "update_p32"));
+        RET_IF(ok(launch_wilson_f32(m, p, nullptr, v, nrhs, 0, EPI_DOT, sc, rhat, part_w, status, M_ACTIVE, s), "w32_dot"));
+      }
       RET_IF(ok(launch_bicg_finalize(FIN_ALPHA, part_w, nbw, sc, status, nullptr, 0, nrhs, s), "fin_alpha"));
-      RET_IF(ok(launch_wilson_f32(m, r, v, t, nrhs, 0, EPI_TSTT, sc, nullptr, part_w, status, M_ACTIVE, s), "w32_tstt"));
+      if (half)
+        RET_IF(ok(launch_wilson_f16(h, h->links16, v16, r, t16, nrhs, 0, EPI_TSTT, sc, nullptr, part_w, status, M_ACTIVE, s), "w16_tstt"));
+      else
+        RET_IF(ok(launch_wilson_f32(m, r, v, t, nrhs, 0, EPI_TSTT, sc, nullptr, part_w, status, M_ACTIVE, s), "w32_tstt"));
       RET_IF(ok(launch_bicg_finalize(FIN_OMEGA, part_w, nbw, sc, status, nullptr, 0, nrhs, s), "fin_omega"));
-      RET_IF(ok(launch_bicg32_update_xr(xs, r, p, v, t, rhat, sc, status, part_s, n4, nrhs, s), "update_xr32"));
+      if (half)
+        RET_IF(ok(launch_bicg16_update_xr(xs, r, p16, v16, t16, rhat, sc, status, part_s, V, nrhs, s), "update_xr16"));
+      else
+        RET_IF(ok(launch_bicg32_update_xr(xs, r, p, v, t, rhat, sc, status, part_s, n4, nrhs, s), "update_xr32"));
       RET_IF(ok(launch_bicg_finalize(FIN_RHO, part_s, nbs, sc, status, nullptr, 0, nrhs, s), "fin_rho"));
     }
     return WD_OK;

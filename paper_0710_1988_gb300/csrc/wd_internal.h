@@ -64,6 +64,9 @@ bool is_device_pointer(const void *p);
 
 }  // namespace wd
 
+// Autotuner slots: nrhs = 1..WD_TUNE_SLOTS-2 each, larger nrhs share the last.
+#define WD_TUNE_SLOTS 34
+
 // The handle.
 struct wd_context {
   int dims[4];
@@ -76,9 +79,17 @@ struct wd_context {
   cudaMemPool_t pool;  // this handle's scratch pool
   wd::Profiler prof;   // optional kernel timing
   float4 *links32;     // FP32 rows 0, 1 of every link (mixed precision), lazily built
+  uint2 *links16;      // FP16 rows 0, 1 of every link, lazily built
+  int mixed_bits;      // storage of the mixed solver's Krylov vectors: 32 or 16
   cudaStream_t side;   // non-blocking stream for graph capture when the caller
                        // passes the legacy default stream; lazily created
   cudaEvent_t ev_in, ev_out;
+  int tune_R[WD_TUNE_SLOTS];   // autotuned FP32 launch shape per nrhs (0: not tuned)
+  int tune_T[WD_TUNE_SLOTS];
+  float tune_ms[WD_TUNE_SLOTS];
+  int tune16_R[WD_TUNE_SLOTS];  // the same for the FP16-storage kernel
+  int tune16_T[WD_TUNE_SLOTS];
+  float tune16_ms[WD_TUNE_SLOTS];
   int eo;              // 1: the operator is the even-odd Schur complement on even sites
   double2 *eo_tmp;     // odd half-vector scratch of the Schur operator
   size_t eo_tmp_cap;   // complex numbers

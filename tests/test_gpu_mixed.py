@@ -142,3 +142,32 @@ def test_mixed_full_size_16x16x16x16(wdl):
     assert rc == 0 and all(s["converged"] and s["true_rel_res"] <= 1e-10 for s in sts)
     assert rel_residual(U, cfg.dims, kappa, host(X)[0], Bh[0]) <= 1.05e-10
     op.close()
+
+
+@pytest.mark.parametrize("R", [1, 2, 4])
+@pytest.mark.parametrize("threads", [64, 128, 256])
+def test_every_f32_launch_shape(wdl, R, threads):
+    import torch
+    dims, nrhs = (6, 4, 2, 8), 5
+    U = L.gauge_field(dims, 0.5, 710)
+    psi = L.gaussian_spinor(dims, 711, nrhs=nrhs)
+    op = wdl.WilsonOperator(dims, cuda(U), 0.13, 0.02)
+    op.set_f32_shape(nrhs, R, threads)
+    out = torch.empty(psi.size, dtype=torch.complex128, device="cuda:0")
+    op.apply_f32(cuda(psi), out)
+    got = host(out).reshape(psi.shape)
+    for r in range(nrhs):
+        ref = dirac.apply_A(U, psi[r], dims, 0.13, 0.02)
+        assert np.abs(got[r] - ref).max() <= 2e-6 * np.abs(ref).max()
+    op.close()
+
+
+def test_autotuner_picks_a_shape_and_solves(wdl, cfg0):
+    c = cfg0
+    op = wdl.WilsonOperator(c["cfg"].dims, cuda(c["U"]), c["kappa"])
+    R, T, ms = op.autotune_f32(3)
+    assert R in (1, 2) and T in (64, 128, 256) and ms > 0
+    X = cuda(np.zeros_like(c["B"]))
+    rc, sts = op.dbicgstab_mixed(cuda(c["B"]), X, None, tol=1e-10)
+    assert rc == 0 and all(s["converged"] for s in sts)
+    op.close()
