@@ -80,7 +80,7 @@ def kappa_c_krylov(links, dims, steps: int = 300, seed: int = 7) -> float:
     for j in range(steps):
         w = dirac.hopping(links, Q[j].reshape(v, 4, 3), dims).ravel()
         for _ in range(2):
-            h = Q[: j + 1].conj() @ w
+            h = (Q[: j + 1] @ w.conj()).conj()  # Q^dagger w without a conjugated copy of Q
             w = w - Q[: j + 1].T @ h
             H[: j + 1, j] += h
         H[j + 1, j] = np.linalg.norm(w)
@@ -94,10 +94,14 @@ def kappa_c_krylov(links, dims, steps: int = 300, seed: int = 7) -> float:
 
 def kappa_c(links, dims) -> float:
     """Dense spectrum up to n = 3072; implicitly restarted Arnoldi up to
-    n = 1e5; a 300-step Arnoldi factorisation beyond."""
+    n = 1e5; a 300-step Arnoldi factorisation up to n = 4e6 and a 200-step
+    one beyond (the basis of (steps + 1) n complex numbers must fit in host
+    memory: 26 GB at 24^3 x 48)."""
     n = 12 * links.shape[0]
     if n <= 3072:
         return kappa_c_dense(links, dims)
     if n <= 100_000:
         return kappa_c_arnoldi(links, dims, tol=1e-10, ncv=100, nev=6)
-    return kappa_c_krylov(links, dims, steps=300)
+    if n <= 4_000_000:
+        return kappa_c_krylov(links, dims, steps=300)
+    return kappa_c_krylov(links, dims, steps=200)

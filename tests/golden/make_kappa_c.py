@@ -33,7 +33,9 @@ def main(names):
                        "link_seed": L.link_seed(cfg), "kappa_c": kc,
                        "method": ("dense eig" if 12 * U.shape[0] <= 3072 else
                                   "Arnoldi (eigs LR, tol 1e-10)" if 12 * U.shape[0] <= 100_000
-                                  else "300-step Arnoldi factorisation, rightmost Ritz value")}
+                                  else "300-step Arnoldi factorisation, rightmost Ritz value"
+                                  if 12 * U.shape[0] <= 4_000_000
+                                  else "200-step Arnoldi factorisation, rightmost Ritz value")}
         print(f"{name}: kappa_c = {kc!r}  ({time.time() - t0:.0f} s)", flush=True)
         with open(OUT, "w") as f:
             json.dump(table, f, indent=1, sort_keys=True)
