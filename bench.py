@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--storage", type=int, default=32, choices=[32, 16],
+                    help="Krylov vector storage of the mixed workloads")
     return ap.parse_args()
 
 
@@ -436,6 +438,14 @@ def main():
     import torch
     if world > 1:
         torch.distributed.init_process_group(backend="nccl")
+    kind = workload_kind(cfg)
+    if kind != "fp64":
+        line = ROW_ARMS[kind](args, cfg, rank, world, local_rank)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
     res = gpu_arm(args, cfg, rank, world, local_rank)
     if rank != 0:
         if world > 1:
@@ -473,7 +483,7 @@ def main():
         "e2e": res["e2e"],
         "counts": res["counts"],
         "mixed_precision": res["mixed"],
-        "kernel_breakdown_ms": {k: v for k, v in res["prof_all"].items() if k != "dslash_site_updates"},
+        "kernel_breakdown_ms": {k: v for k, v in res["prof_all"].items() if isinstance(v, dict)},
     }
     pa = res["prof_all"]
     line["gpu_launches"] = int(sum(pa[c]["launches"] for c in ("dslash", "stream", "tall_skinny", "dense")) * steps)
@@ -495,6 +505,321 @@ def main():
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------------ the other workloads
+#
+# The default workload above is the benchmark line.  The presets below are the
+# workloads of the growth rows (mixed precision at 20^3x32, twisted-mass
+# shifts at 24^3x48, differentiation at 32^3x64); `--config <preset>` runs one
+# of them with the same timing rules (warm-up steps, L2 flush, CUDA events on
+# the launching stream, clocks sampled, max over ranks) and prints its own
+# JSON line.
+
+# FP32 / FP16 bytes per site and system of the mixed solver's kernels
+LOW_DSLASH_BYTES = {32: 3 * 96, 16: 52 + 52 + 96}   # in + out + (r_hat or r) per site update
+LOW_LINK_BYTES = {32: 4 * 48, 16: 4 * 24}            # links, read once per launch
+LOW_UPDATE_BYTES = {32: 4 * 96 + 8 * 96,             # p = r + beta (p - omega v); x, r update
+                    16: (96 + 3 * 52) + (4 * 96 + 3 * 52 + 2 * 96)}
+
+
+def workload_kind(cfg):
+    if cfg.mus:
+        return "twisted"
+    if cfg.name.startswith("grad_"):
+        return "grad"
+    if cfg.name.endswith("_mixed"):
+        return "mixed"
+    return "fp64"
+
+
+def timed_steps(args, step, op, flush, stream, world, dev, prof_mask=0):
+    """W warm-up steps, then K steps timed with CUDA events on `stream` (L2
+    flushed before each), clocks sampled; returns per-step ms, the last
+    step's result, the profile of the timed region and the clock summary."""
+    import torch
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    op.profile(mask=prof_mask)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ms_steps, last = [], None
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        last = step()
+        e1.record(stream)
+        e1.synchronize()
+        ms_steps.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    prof = op.profile_read()
+    op.profile(mask=0)
+    return ms_steps, last, prof, clocks.stop()
+
+
+def low_rooflines(prof, bits, V, peaks, iters_total):
+    """HBM rooflines of the mixed solver's FP32/FP16 kernels from a profiled
+    step: the Wilson apply (site updates counted on the device) and the two
+    per-iteration vector updates (one pass of each per system iteration)."""
+    hbm = peaks.get("hbm_gbs")
+    out = {}
+    d = prof["dslash_low"]
+    if d["launches"]:
+        byt = LOW_DSLASH_BYTES[bits] * prof["dslash_low_site_updates"] + LOW_LINK_BYTES[bits] * V * d["launches"]
+        gbs = byt / (d["ms"] * 1e-3) / 1e9
+        out["dslash"] = {"kernel": f"wilson_f{bits}_kernel", "bound": "hbm", "achieved": round(gbs, 1),
+                         "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4) if hbm else None,
+                         "traffic": None, "avg_launch_ms": d["ms"] / d["launches"],
+                         "launches": d["launches"],
+                         "algorithmic_bytes_per_launch": byt / d["launches"]}
+    u = prof["stream_low"]
+    if u["launches"]:
+        byt = LOW_UPDATE_BYTES[bits] * V * iters_total
+        gbs = byt / (u["ms"] * 1e-3) / 1e9
+        out["updates"] = {"kernel": f"bicg{bits}_update_p + bicg{bits}_update_xr", "bound": "hbm",
+                          "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                          "frac": round(gbs / hbm, 4) if hbm else None, "traffic": None,
+                          "avg_launch_ms": u["ms"] / u["launches"], "launches": u["launches"],
+                          "algorithmic_bytes_per_launch": byt / u["launches"]}
+    return out
+
+
+def _row_line(cfg, args, world, value, unit, total_ms, dtype, workload, extra):
+    line = {"metric": METRIC if unit == "solves/s" else f"{unit} at rel. residual {cfg.tol:g}",
+            "value": round(value, 4), "unit": unit, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": f"synthetic: SU(3) links exp(i*{cfg.eps}*H) (seed {L.link_seed(cfg)}), "
+                    f"{cfg.rhs_kind} sources; no dataset",
+            "config": {"workload": workload, "lattice": list(cfg.dims),
+                       "parallelism": f"replicas x{world}",
+                       "l2": "256 MB L2 flush before every step; vectors exceed the 129 MB L2"}}
+    line.update(extra)
+    return line
+
+
+def mixed_arm(args, cfg, rank, world, local_rank):
+    """20^3x32: GMRES-DR(80,60) (FP64) on one Z4 source, then D-BiCGStab(60)
+    with the FP32 (or FP16) iteration and FP64 reliable updates every 50
+    iterations on 12 Z4 sources, all to 1e-10 true residual."""
+    import torch
+    import paper_0710_1988_gb300 as wdl
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    kappa = kappa_for(cfg)
+    U = L.gauge_field(cfg.dims, cfg.eps, L.link_seed(cfg))
+    v = L.volume(cfg.dims)
+    n = 12 * v
+    src = rank_sources(cfg, rank, cfg.n_rhs + 1)
+    b0 = torch.from_numpy(src[0].ravel()).to(dev)
+    B = torch.from_numpy(src[1:].reshape(cfg.n_rhs, n)).to(dev)
+    x0 = torch.zeros_like(b0)
+    X = torch.zeros_like(B)
+    V = torch.zeros(cfg.k * n, dtype=torch.complex128, device=dev)
+    op = wdl.WilsonOperator(cfg.dims, torch.from_numpy(U).to(dev), kappa)
+    op.set_mixed_storage(args.storage)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        x0.zero_()
+        X.zero_()
+        rc, st, _, _ = op.gmresdr(b0, x0, cfg.m, cfg.k, cfg.tol, 400000, V_out=V)
+        defl = op.deflation(V, cfg.k)
+        rc2, sts = op.dbicgstab_mixed(B, X, defl, tol=cfg.tol, reliable_every=50)
+        defl.close()
+        if rc != 0 or rc2 != 0 or not all(q["converged"] for q in sts):
+            raise RuntimeError(f"solve did not converge: gmresdr rc={rc}, mixed rc={rc2}")
+        return st, sts
+
+    ms_steps, last, _, clk = timed_steps(args, step, op, flush, stream, world, dev)
+    total_ms = max_over_ranks(sum(ms_steps), dev)
+    st, sts = last
+    # one profiled step (graphs off while profiling): breakdown and rooflines
+    op.profile(mask=0x3F)
+    st_p, sts_p = step()
+    prof = op.profile_read()
+    op.profile(mask=0)
+    peaks = load_json(MEASURED_PEAKS, {}) or {}
+    roof = low_rooflines(prof, args.storage, v, peaks, sum(q["iters"] for q in sts_p))
+    # D-BiCGStab alone: FP64 against FP32 and FP16 storage, same V and sources
+    defl = op.deflation(V, cfg.k)
+    comp = {}
+    for name, bits in (("fp64", None), ("mixed32", 32), ("mixed16", 16)):
+        if bits:
+            op.set_mixed_storage(bits)
+        fn = op.dbicgstab if bits is None else (
+            lambda B_, X_, d_, tol: op.dbicgstab_mixed(B_, X_, d_, tol=tol, reliable_every=50))
+        X.zero_()
+        fn(B, X, defl, tol=cfg.tol)
+        X.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc, ss = fn(B, X, defl, tol=cfg.tol)
+        e1.record(stream)
+        e1.synchronize()
+        if rc != 0 or not all(q["converged"] for q in ss):
+            raise RuntimeError(f"{name} D-BiCGStab did not converge")
+        comp[name] = {"solves_per_s": round(cfg.n_rhs / (e0.elapsed_time(e1) * 1e-3), 3),
+                      "iters": [q["iters"] for q in ss],
+                      "max_true_rel_res": max(q["true_rel_res"] for q in ss)}
+    defl.close()
+    op.set_mixed_storage(args.storage)
+    for name in ("mixed32", "mixed16"):
+        comp[name]["speedup_vs_fp64"] = round(comp[name]["solves_per_s"] / comp["fp64"]["solves_per_s"], 3)
+    op.close()
+    extra = {
+        "gpu_launches": None,
+        "roofline": roof.get("updates"),
+        "roofline_dslash": roof.get("dslash"),
+        "clocks": clk,
+        "e2e": None,
+        "counts": {"gmresdr_mvp": st["mvp"], "gmresdr_cycles": st["cycles"],
+                   "dbicgstab_iters": [q["iters"] for q in sts],
+                   "true_rel_res_max": max(q["true_rel_res"] for q in sts)},
+        "dbicgstab_alone": comp,
+        "kernel_breakdown_ms": {k: v_ for k, v_ in prof.items() if isinstance(v_, dict)},
+    }
+    extra["gpu_launches"] = int(sum(c["launches"] for c in extra["kernel_breakdown_ms"].values()))
+    return _row_line(cfg, args, world, cfg.n_rhs * args.steps * world / (total_ms * 1e-3),
+                     "solves/s", total_ms, f"f{args.storage} iteration, f64 reliable updates",
+                     f"{cfg.name}: GMRES-DR({cfg.m},{cfg.k}) FP64 on 1 Z4 source + D-BiCGStab("
+                     f"{cfg.k}) mixed (FP{args.storage} storage, FP64 reliable updates every 50) "
+                     f"on {cfg.n_rhs} Z4 sources, tol {cfg.tol:g}, kappa = {cfg.kappa_factor} kappa_c",
+                     extra)
+
+
+def twisted_arm(args, cfg, rank, world, local_rank):
+    """24^3x48 twisted mass at kappa_c: the Sec. 4 shifts heaviest first, each
+    projected over the earlier solutions, 16 Gaussian sources per shift in one
+    batch, mixed-precision BiCGStab."""
+    import torch
+    import paper_0710_1988_gb300 as wdl
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    kappa = kappa_for(cfg)
+    U = L.gauge_field(cfg.dims, cfg.eps, L.link_seed(cfg))
+    v = L.volume(cfg.dims)
+    n = 12 * v
+    mus = sorted(cfg.mus, reverse=True)
+    B = torch.from_numpy(rank_sources(cfg, rank, cfg.n_rhs).reshape(cfg.n_rhs, n)).to(dev)
+    X = torch.zeros(len(mus) * cfg.n_rhs * n, dtype=torch.complex128, device=dev)
+    op = wdl.WilsonOperator(cfg.dims, torch.from_numpy(U).to(dev), kappa)
+    op.set_mixed_storage(args.storage)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def run(project):
+        X.zero_()
+        rc, sts = op.multishift(B, X, mus, tol=cfg.tol, project=project, mixed=True)
+        if rc != 0 or not all(q["converged"] for row in sts for q in row):
+            raise RuntimeError(f"twisted-mass shifts did not converge (status {rc})")
+        return sts
+
+    ms_steps, sts, _, clk = timed_steps(args, lambda: run(True), op, flush, stream, world, dev)
+    total_ms = max_over_ranks(sum(ms_steps), dev)
+    op.profile(mask=0x3F)
+    sts_p = run(True)
+    prof = op.profile_read()
+    op.profile(mask=0)
+    peaks = load_json(MEASURED_PEAKS, {}) or {}
+    roof = low_rooflines(prof, args.storage, v, peaks, sum(q["iters"] for row in sts_p for q in row))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sts_np = run(False)
+    e1.record(stream)
+    e1.synchronize()
+    op.close()
+    per_shift = []
+    for i, mu in enumerate(mus):
+        per_shift.append({"mu": mu,
+                          "mvp_projected": [q["mvp"] + q["mvp_extra"] for q in sts[i]],
+                          "mvp_unprojected": [q["mvp"] + q["mvp_extra"] for q in sts_np[i]],
+                          "max_true_rel_res": max(q["true_rel_res"] for q in sts[i])})
+    units = cfg.n_rhs * len(mus)
+    extra = {
+        "gpu_launches": None,
+        "roofline": roof.get("updates"),
+        "roofline_dslash": roof.get("dslash"),
+        "clocks": clk,
+        "e2e": None,
+        "shifts": per_shift,
+        "unprojected_solves_per_s": round(units / (e0.elapsed_time(e1) * 1e-3), 3),
+        "kernel_breakdown_ms": {k: v_ for k, v_ in prof.items() if isinstance(v_, dict)},
+    }
+    extra["gpu_launches"] = int(sum(c["launches"] for c in extra["kernel_breakdown_ms"].values()))
+    return _row_line(cfg, args, world, units * args.steps * world / (total_ms * 1e-3), "solves/s",
+                     total_ms, f"f{args.storage} iteration, f64 reliable updates",
+                     f"{cfg.name}: A_W + i mu gamma5 at kappa_c, shifts {mus} heaviest first, each "
+                     f"projected over the earlier solutions (Sec. 4), {cfg.n_rhs} Gaussian sources "
+                     f"per shift batched, mixed BiCGStab to {cfg.tol:g}; value counts (source, shift) "
+                     f"pairs", extra)
+
+
+def grad_arm(args, cfg, rank, world, local_rank):
+    """Differentiation: x = A^-1 b forward (FP64 BiCGStab) and the backward of
+    L = Re(eta^dagger x) through the autograd Function (adjoint solve via
+    gamma5, dL/db, dL/dkappa and the link force), 1e-10."""
+    import torch
+    import paper_0710_1988_gb300 as wdl
+    from paper_0710_1988_gb300.autograd import wilson_solve
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    kappa = kappa_for(cfg)
+    U = L.gauge_field(cfg.dims, cfg.eps, L.link_seed(cfg))
+    v = L.volume(cfg.dims)
+    src = rank_sources(cfg, rank, 2)
+    b = torch.from_numpy(src[0].ravel()).to(dev)
+    eta = torch.from_numpy(src[1].ravel()).to(dev)
+    op = wdl.WilsonOperator(cfg.dims, torch.from_numpy(U).to(dev), kappa)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        bt = b.clone().requires_grad_(True)
+        kt = torch.tensor(kappa, dtype=torch.float64, requires_grad=True)
+        om = torch.zeros((v, 4, 8), dtype=torch.float64, device=dev, requires_grad=True)
+        x = wilson_solve(bt, kt, om, op, None, cfg.tol)
+        loss = (eta.conj() * x).sum().real
+        loss.backward()
+        return float(kt.grad), float(om.grad.abs().max())
+
+    ms_steps, last, prof_live, clk = timed_steps(args, step, op, flush, stream, world, dev,
+                                                 prof_mask=0x1)
+    total_ms = max_over_ranks(sum(ms_steps), dev)
+    op.profile(mask=0x3F)
+    step()
+    prof = op.profile_read()
+    op.profile(mask=0)
+    op.close()
+    peaks = load_json(MEASURED_PEAKS, {}) or {}
+    fp64_peak = {"tflops": round(FP64_FLOPS_PER_CLK_PER_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12, 4),
+                 "source": "derived: 4 FP64 flops/clk/SM x 152 SMs x 2070 MHz"}
+    r = roofline({"prof_live": prof_live}, peaks, fp64_peak)
+    r["traffic"] = None
+    r.pop("traffic_source", None)
+    extra = {"gpu_launches": int(sum(c["launches"] for c in prof.values() if isinstance(c, dict))),
+             "roofline": r, "clocks": clk, "e2e": None,
+             "dkappa": last[0], "max_abs_force": last[1],
+             "kernel_breakdown_ms": {k: v_ for k, v_ in prof.items() if isinstance(v_, dict)}}
+    return _row_line(cfg, args, world, args.steps * world / (total_ms * 1e-3),
+                     "fwd+bwd solves/s", total_ms, "f64",
+                     f"{cfg.name}: x = A^-1 b (BiCGStab) and the backward of Re(eta^dagger x) "
+                     f"(adjoint solve via gamma5, dL/db, dL/dkappa, link force), tol {cfg.tol:g}, "
+                     f"kappa = {cfg.kappa_factor} kappa_c", extra)
+
+
+ROW_ARMS = {"mixed": mixed_arm, "twisted": twisted_arm, "grad": grad_arm}
 
 
 def reference_arm(args, cfg, rank, world):

@@ -287,14 +287,18 @@ int wd_apply_f32_noalloc(wd_handle h, const void *in, void *out, int nrhs,
 
 /* Kernel timing, not part of the paper's method: CUDA events bracket every
  * launch of the enabled categories on the launching stream.  Categories:
- * 0 Wilson apply (dslash), 1 streaming vector kernels and scalar
+ * 0 FP64 Wilson apply (dslash), 1 streaming vector kernels and scalar
  * finalizers, 2 tall-skinny products (V^dagger W, W += V Y), 3 single-block
- * dense kernels (LU, GMRES-DR cycle end). */
+ * dense kernels (LU, GMRES-DR cycle end), 4 FP32/FP16 Wilson apply of the
+ * mixed solver, 5 its two per-iteration vector updates (p, and x with r).
+ * While any category is on, the mixed solver launches its kernels one by
+ * one instead of replaying CUDA graphs. */
 typedef struct {
-  long long launches[4];
-  double ms[4];                    /* summed launch durations */
-  long long dslash_site_updates;   /* lattice sites x systems the dslash
-                                      launches actually processed */
+  long long launches[6];
+  double ms[6];                        /* summed launch durations */
+  long long dslash_site_updates;       /* lattice sites x systems the FP64
+                                          dslash launches processed */
+  long long dslash_low_site_updates;   /* the same for category 4 */
 } wd_profile;
 
 /* Enable the categories whose bit is set in mask (0 disables) and reset the

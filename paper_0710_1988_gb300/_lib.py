@@ -41,17 +41,19 @@ class WdStats(ctypes.Structure):
 
 class WdProfile(ctypes.Structure):
     _fields_ = [
-        ("launches", ctypes.c_longlong * 4),
-        ("ms", ctypes.c_double * 4),
+        ("launches", ctypes.c_longlong * 6),
+        ("ms", ctypes.c_double * 6),
         ("dslash_site_updates", ctypes.c_longlong),
+        ("dslash_low_site_updates", ctypes.c_longlong),
     ]
 
-    CATEGORIES = ("dslash", "stream", "tall_skinny", "dense")
+    CATEGORIES = ("dslash", "stream", "tall_skinny", "dense", "dslash_low", "stream_low")
 
     def as_dict(self):
         return {c: {"launches": int(self.launches[i]), "ms": float(self.ms[i])}
                 for i, c in enumerate(self.CATEGORIES)} | {
-            "dslash_site_updates": int(self.dslash_site_updates)}
+            "dslash_site_updates": int(self.dslash_site_updates),
+            "dslash_low_site_updates": int(self.dslash_low_site_updates)}
 
 
 P = ctypes.c_void_p

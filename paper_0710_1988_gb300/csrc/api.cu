@@ -66,7 +66,7 @@ void Profiler::reset() {
     launches[c] = 0;
     ms[c] = 0.0;
   }
-  if (d_sites) cudaMemset(d_sites, 0, sizeof(unsigned long long));
+  if (d_sites) cudaMemset(d_sites, 0, 2 * sizeof(unsigned long long));
 }
 
 void Profiler::destroy() {
@@ -154,8 +154,8 @@ extern "C" int wd_create(const int lat[4], const void *links, double kappa, doub
   h->pool = nullptr;
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = cudaMalloc(&h->links, sizeof(double2) * 36 * V);
-  if (e == cudaSuccess) e = cudaMalloc(&h->prof.d_sites, sizeof(unsigned long long));
-  if (e == cudaSuccess) e = cudaMemset(h->prof.d_sites, 0, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&h->prof.d_sites, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(h->prof.d_sites, 0, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess)
     e = cudaMemcpy(h->links, links, sizeof(double2) * 36 * V, cudaMemcpyDefault);
   if (e == cudaSuccess) {
@@ -267,10 +267,11 @@ extern "C" int wd_profile_read(wd_handle h, wd_profile *out) {
     out->launches[c] = h->prof.launches[c];
     out->ms[c] = h->prof.ms[c];
   }
-  unsigned long long sites = 0;
-  cudaError_t e = cudaMemcpy(&sites, h->prof.d_sites, sizeof(sites), cudaMemcpyDeviceToHost);
+  unsigned long long sites[2] = {0, 0};
+  cudaError_t e = cudaMemcpy(sites, h->prof.d_sites, sizeof(sites), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "wd_profile_read");
-  out->dslash_site_updates = (long long)sites;
+  out->dslash_site_updates = (long long)sites[0];
+  out->dslash_low_site_updates = (long long)sites[1];
   return WD_OK;
 }
 

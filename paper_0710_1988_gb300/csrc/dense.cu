@@ -374,17 +374,18 @@ __device__ int schur_block(double2 *A, double2 *Z, int m, int ld, double2 *u, lo
   const double anorm = part > 0.0 ? part : 1.0;
   if (clk != nullptr && tid == 0) clk[7] = clock64();
   // Shifted QR iteration.  Within a sweep only the active block
-  // [l..hi] x [l..hi] is updated rotation by rotation, two barriers per
+  // [l..hi] x [l..hi] is updated rotation by rotation, one barrier per
   // rotation.  Lane 0 of the last warp (rt) computes the shift and every
-  // rotation and owns the rows kk+1..kk+2 of each column update, whose new
-  // entries give the next rotation; the other warps update everything else.
+  // rotation and applies each rotation to the few entries the next one
+  // depends on; the other warps apply it everywhere else at the same time.
   // The parts of T outside the active block and the Schur vectors Z receive
   // the sweep's rotations afterwards, one thread per row or column.
   __shared__ double s_gc[CE_MAXM];
   __shared__ double2 s_gs[CE_MAXM];
   __shared__ int s_l[2];    // deflation point of the scan, double-buffered
-  const int rt = bd - 32;   // rotation thread
-  const int nwk = bd - 32;  // threads of the bulk updates
+  const int rt = bd - 32;   // first thread of the rotation warp (the last warp)
+  const int nwk = bd - 64;  // threads of the bulk updates (all warps but 3 and the last)
+  const int wid = tid >> 5, lane = tid & 31;
   long long rotations = 0, t_scan = 0, t_rot = 0, t_def = 0, t0 = 0;
   int hi = m - 1, its = 0, total = 0, scan = 0;
   if (tid < 2) s_l[tid] = 0;
@@ -438,34 +439,65 @@ __device__ int schur_block(double2 *A, double2 *Z, int m, int ld, double2 *u, lo
       givens(csub(A[l * ld + l], sigma), A[(l + 1) * ld + l], s_gc[l], s_gs[l]);
     }
     for (int kk = l; kk < hi; ++kk) {
-      __syncthreads();  // rotation kk published; previous column update done
+      __syncthreads();  // rotation kk published; the updates of rotation kk - 1 done
       const double gc = s_gc[kk];
       const double2 gs = s_gs[kk];
-      const double2 mgs = cneg(cconj(gs));
-      const int c0 = kk > l ? kk - 1 : l;
-      if (tid < nwk) {
-        for (int j = c0 + tid; j <= hi; j += nwk) {
-          const double2 a1 = A[kk * ld + j], a2 = A[(kk + 1) * ld + j];
-          A[kk * ld + j] = cadd(cscale(gc, a1), cmul(gs, a2));
-          A[(kk + 1) * ld + j] = (kk > l && j == kk - 1) ? make_double2(0.0, 0.0)
-                                                         : cadd(cmul(mgs, a1), cscale(gc, a2));
+      const double2 mgs = cneg(cconj(gs)), cgs = cconj(gs), ngs = cneg(gs);
+      if (tid >= rt) {
+        // Rotation warp: the entries the next rotation depends on, one per
+        // lane (an FP64 instruction occupies the warp's pipe for the same time
+        // whether 1 or 32 lanes are active, so serial work is spread over
+        // lanes).  Lanes 0..3: row rotation on the 2 x 2 block (kk, kk+1)^2;
+        // then lanes 0..5: column rotation on rows kk..kk+2; then lane 0
+        // forms the next rotation from column kk.
+        const int ln = tid - rt;
+        double2 v = make_double2(0.0, 0.0);
+        if (ln < 4) {
+          const int j = kk + (ln & 1);
+          const double2 t0 = A[kk * ld + j], t1 = A[(kk + 1) * ld + j];
+          v = (ln < 2) ? cadd(cscale(gc, t0), cmul(gs, t1)) : cadd(cmul(mgs, t0), cscale(gc, t1));
+        } else if (ln < 6 && kk + 2 <= hi) {
+          v = A[(kk + 2) * ld + kk + (ln - 4)];
         }
-      }
-      __syncthreads();
-      const int rmax = kk + 2 < hi ? kk + 2 : hi;
-      const double2 cgs = cconj(gs), ngs = cneg(gs);
-      if (tid == rt) {
-        for (int row = kk + 1; row <= rmax; ++row) {
-          const double2 a1 = A[row * ld + kk], a2 = A[row * ld + kk + 1];
-          A[row * ld + kk] = cadd(cscale(gc, a1), cmul(cgs, a2));
-          A[row * ld + kk + 1] = cadd(cmul(ngs, a1), cscale(gc, a2));
-        }
-        if (kk + 1 < hi) givens(A[(kk + 1) * ld + kk], A[(kk + 2) * ld + kk], s_gc[kk + 1], s_gs[kk + 1]);
-      } else if (tid < nwk) {
-        for (int row = l + tid; row <= kk; row += nwk) {
-          const double2 a1 = A[row * ld + kk], a2 = A[row * ld + kk + 1];
-          A[row * ld + kk] = cadd(cscale(gc, a1), cmul(cgs, a2));
-          A[row * ld + kk + 1] = cadd(cmul(ngs, a1), cscale(gc, a2));
+        const int base = ln & ~1;
+        double2 p0, p1;
+        p0.x = __shfl_sync(0xffffffffu, v.x, base & 31);
+        p0.y = __shfl_sync(0xffffffffu, v.y, base & 31);
+        p1.x = __shfl_sync(0xffffffffu, v.x, (base + 1) & 31);
+        p1.y = __shfl_sync(0xffffffffu, v.y, (base + 1) & 31);
+        const double2 o = (ln & 1) == 0 ? cadd(cscale(gc, p0), cmul(cgs, p1))
+                                        : cadd(cmul(ngs, p0), cscale(gc, p1));
+        if (ln < 4 || (ln < 6 && kk + 2 <= hi)) A[(kk + (ln >> 1)) * ld + kk + (ln & 1)] = o;
+        double2 x, y;
+        x.x = __shfl_sync(0xffffffffu, o.x, 2);
+        x.y = __shfl_sync(0xffffffffu, o.y, 2);
+        y.x = __shfl_sync(0xffffffffu, o.x, 4);
+        y.y = __shfl_sync(0xffffffffu, o.y, 4);
+        if (ln == 0 && kk + 1 < hi) givens(x, y, s_gc[kk + 1], s_gs[kk + 1]);
+      } else if (wid != 3) {
+        // Everything else of rotation kk, concurrently, on warps 0-2 and 4-6
+        // (warp 3 idles so that the rotation warp's FP64 pipe is not shared,
+        // with warps assigned to the four schedulers round-robin): the row
+        // rotation on rows kk, kk+1 in the columns other than kk, kk+1
+        // (c0..kk-1 and kk+2..hi; the bulge entry (kk+1, kk-1) becomes 0), and
+        // the column rotation on rows l..kk-1.  The rotation warp's entries
+        // are disjoint from these.
+        const int wk = (wid < 3 ? wid : wid - 1) * 32 + lane;
+        const int c0 = kk > l ? kk - 1 : l;
+        const int ncols = hi - c0 - 1, nrows = kk - l;
+        for (int t = wk; t < ncols + nrows; t += nwk) {
+          if (t < ncols) {
+            const int j = c0 + t < kk ? c0 + t : c0 + t + 2;
+            const double2 a1 = A[kk * ld + j], a2 = A[(kk + 1) * ld + j];
+            A[kk * ld + j] = cadd(cscale(gc, a1), cmul(gs, a2));
+            A[(kk + 1) * ld + j] = (kk > l && j == kk - 1) ? make_double2(0.0, 0.0)
+                                                           : cadd(cmul(mgs, a1), cscale(gc, a2));
+          } else {
+            const int row = l + (t - ncols);
+            const double2 a1 = A[row * ld + kk], a2 = A[row * ld + kk + 1];
+            A[row * ld + kk] = cadd(cscale(gc, a1), cmul(cgs, a2));
+            A[row * ld + kk + 1] = cadd(cmul(ngs, a1), cscale(gc, a2));
+          }
         }
       }
     }

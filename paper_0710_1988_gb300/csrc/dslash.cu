@@ -50,15 +50,82 @@ __device__ __forceinline__ void load_spinor(const double2 *__restrict__ p, doubl
   for (int i = 0; i < 12; ++i) v[i] = __ldg(p + i);
 }
 
-template <int MU, int S, bool ADJ>
-__device__ __forceinline__ void hop(const double2 *__restrict__ psi,
-                                    const double2 *__restrict__ links, long long q,
-                                    long long ql, double2 (&acc)[12]) {
-  double2 p[12], h[6], c[6];
-  load_spinor(psi + 12 * q, p);
-  project<MU, S>(p, h);
-  su3_mul<ADJ>(links + (ql * 4 + MU) * 9, h, c);
-  reconstruct<MU, S>(acc, c);
+// out = init + U^dagger h: the product accumulates onto init in its FMA chain.
+__device__ __forceinline__ void su3_adj_mul_acc(const double2 *__restrict__ u,
+                                                const double2 (&h)[6], const double2 (&init)[6],
+                                                double2 (&out)[6]) {
+  double2 m[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) m[i] = __ldg(u + i);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) {
+      double2 acc = init[3 * sp + a];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) acc = cfmac(m[3 * b + a], h[3 * sp + b], acc);
+      out[3 * sp + a] = acc;
+    }
+}
+
+// Both hops of direction MU.  With chi_f = U_MU(x) h_f (forward, projector
+// sign S) and chi_b = U_MU(x - MU)^dagger h_b (backward, sign -S), the pair
+// contributes [chi_f + chi_b ; S B^dagger (chi_f - chi_b)] (the lower spin
+// pair of each hop is S or -S times B^dagger of its upper pair).  The sum is
+// formed by starting chi_b's FMA chain at chi_f and the difference as
+// 2 chi_f - sum, which saves the separate additions of the two hops; FIRST
+// assigns instead of accumulating.
+template <int MU, int S, bool FIRST>
+__device__ __forceinline__ void hop_pair(const double2 *__restrict__ psi,
+                                         const double2 *__restrict__ links, long long qf,
+                                         long long s, long long qb, double2 (&acc)[12]) {
+  double2 sum[6], dif[6];
+  {
+    double2 p[12], h[6], cf[6];
+    load_spinor(psi + 12 * qf, p);
+    project<MU, S>(p, h);
+    su3_mul<false>(links + (s * 4 + MU) * 9, h, cf);
+    load_spinor(psi + 12 * qb, p);
+    project<MU, -S>(p, h);
+    su3_adj_mul_acc(links + (qb * 4 + MU) * 9, h, cf, sum);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+      dif[i] = make_double2(fma(2.0, cf[i].x, -sum[i].x), fma(2.0, cf[i].y, -sum[i].y));
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double2 c0 = dif[a], c1 = dif[3 + a];
+    // B^dagger applied to (c0, c1): rows 6+a and 9+a of the lower spin pair
+    double2 l6, l9;
+    if (MU == 0) {        // B^dagger = (i c1, i c0)
+      l6 = cmuli(c1);
+      l9 = cmuli(c0);
+    } else if (MU == 1) { // (c1, -c0)
+      l6 = c1;
+      l9 = cneg(c0);
+    } else if (MU == 2) { // (i c0, -i c1)
+      l6 = cmuli(c0);
+      l9 = cmulmi(c1);
+    } else {              // (c0, c1)
+      l6 = c0;
+      l9 = c1;
+    }
+    if (S < 0) {
+      l6 = cneg(l6);
+      l9 = cneg(l9);
+    }
+    if (FIRST) {
+      acc[a] = sum[a];
+      acc[3 + a] = sum[3 + a];
+      acc[6 + a] = l6;
+      acc[9 + a] = l9;
+    } else {
+      acc[a] = cadd(acc[a], sum[a]);
+      acc[3 + a] = cadd(acc[3 + a], sum[3 + a]);
+      acc[6 + a] = cadd(acc[6 + a], l6);
+      acc[9 + a] = cadd(acc[9 + a], l9);
+    }
+  }
 }
 
 template <bool DAG, int EPI>
@@ -80,19 +147,12 @@ wilson_f64_kernel(const double2 *__restrict__ links, const double2 *__restrict__
     const long long xp = nb.up[0], xm = nb.dn[0], yp = nb.up[1], ym = nb.dn[1];
     const long long zp = nb.up[2], zm = nb.dn[2], tp = nb.up[3], tm = nb.dn[3];
 
-    constexpr int F = DAG ? +1 : -1;  // projector sign on forward hops
-    constexpr int B = -F;             // and on backward hops
+    constexpr int F = DAG ? +1 : -1;  // projector sign on forward hops (-F on backward)
     double2 acc[12];
-#pragma unroll
-    for (int i = 0; i < 12; ++i) acc[i] = make_double2(0.0, 0.0);
-    hop<0, F, false>(psi, links, xp, s, acc);
-    hop<0, B, true>(psi, links, xm, xm, acc);
-    hop<1, F, false>(psi, links, yp, s, acc);
-    hop<1, B, true>(psi, links, ym, ym, acc);
-    hop<2, F, false>(psi, links, zp, s, acc);
-    hop<2, B, true>(psi, links, zm, zm, acc);
-    hop<3, F, false>(psi, links, tp, s, acc);
-    hop<3, B, true>(psi, links, tm, tm, acc);
+    hop_pair<0, F, true>(psi, links, xp, s, xm, acc);
+    hop_pair<1, F, false>(psi, links, yp, s, ym, acc);
+    hop_pair<2, F, false>(psi, links, zp, s, zm, acc);
+    hop_pair<3, F, false>(psi, links, tp, s, tm, acc);
 
     double2 p[12];
     load_spinor(psi + 12 * s, p);

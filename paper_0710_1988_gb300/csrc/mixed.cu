@@ -131,8 +131,16 @@ wilson_f32_kernel(const float4 *__restrict__ links, const float4 *__restrict__ i
                   const float4 *__restrict__ in2, float4 *__restrict__ out, LatticeGeom g,
                   float kappa, float mu, int nrhs, const BicgScalars *__restrict__ sc,
                   const float4 *__restrict__ aux, double *__restrict__ partial,
-                  const int *__restrict__ status, unsigned mask) {
-  const int r0 = blockIdx.y * R;
+                  const int *__restrict__ status, unsigned mask,
+                  unsigned long long *__restrict__ sites) {
+  // Blocks are numbered system-row fastest: the nrow blocks that cover the
+  // same sites run next to each other and share the links and the
+  // neighbour spinors' cache lines through L2.
+  const int nrow = (nrhs + R - 1) / R;
+  const int row = (int)(blockIdx.x % (unsigned)nrow);
+  const long long sb = blockIdx.x / (unsigned)nrow;   // site block
+  const long long nsb = (g.V + TPB - 1) / TPB;        // site blocks
+  const int r0 = row * R;
   const long long V = g.V;
   bool on[R];
   bool any = false;
@@ -142,11 +150,17 @@ wilson_f32_kernel(const float4 *__restrict__ links, const float4 *__restrict__ i
     any |= on[r];
   }
   if (!any) return;  // uniform over the block
+  if (sites != nullptr && sb == 0 && threadIdx.x == 0) {
+    int cnt = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) cnt += on[r] ? 1 : 0;
+    atomicAdd(sites, (unsigned long long)V * cnt);  // work accounting for the profiler
+  }
   float2 alpha[R];
 #pragma unroll
   for (int r = 0; r < R; ++r)
     alpha[r] = (FUSED && on[r]) ? f2(sc[r0 + r].alpha) : make_float2(0.f, 0.f);
-  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long s = sb * TPB + threadIdx.x;
   float red[R][3];
 #pragma unroll
   for (int r = 0; r < R; ++r) red[r][0] = red[r][1] = red[r][2] = 0.f;
@@ -229,7 +243,7 @@ wilson_f32_kernel(const float4 *__restrict__ links, const float4 *__restrict__ i
         double t = 0.0;
 #pragma unroll
         for (int w2 = 0; w2 < NW; ++w2) t += sh[r][q][w2];
-        partial[((long long)(r0 + r) * gridDim.x + blockIdx.x) * 3 + q] = t;
+        partial[((long long)(r0 + r) * nsb + sb) * 3 + q] = t;
       }
     }
   }
@@ -242,16 +256,18 @@ static cudaError_t launch_w32(const Mixed32 &m, const float4 *in, const float4 *
                               unsigned mask, cudaStream_t s) {
   const wd_context *h = m.h;
   LatticeGeom g = geom_of(h);
-  dim3 grid((unsigned)((h->V + TPB - 1) / TPB), (nrhs + R - 1) / R);
+  const long long nblk = (h->V + TPB - 1) / TPB * ((nrhs + R - 1) / R);
+  if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  const dim3 grid((unsigned)nblk);
   const float kap = (float)h->kappa, mu = (float)h->mu;
   if (epi == EPI_DOT)
-    wilson_f32_kernel<R, TPB, false, EPI_DOT, false><<<grid, TPB, 0, s>>>(m.links, in, nullptr, out, g, kap, mu, nrhs, sc, aux, partial, status, mask);
+    wilson_f32_kernel<R, TPB, false, EPI_DOT, false><<<grid, TPB, 0, s>>>(m.links, in, nullptr, out, g, kap, mu, nrhs, sc, aux, partial, status, mask, m.sites);
   else if (epi == EPI_TSTT)
-    wilson_f32_kernel<R, TPB, false, EPI_TSTT, true><<<grid, TPB, 0, s>>>(m.links, in, in2, out, g, kap, mu, nrhs, sc, aux, partial, status, mask);
+    wilson_f32_kernel<R, TPB, false, EPI_TSTT, true><<<grid, TPB, 0, s>>>(m.links, in, in2, out, g, kap, mu, nrhs, sc, aux, partial, status, mask, m.sites);
   else if (dagger)
-    wilson_f32_kernel<R, TPB, true, EPI_NONE, false><<<grid, TPB, 0, s>>>(m.links, in, nullptr, out, g, kap, mu, nrhs, sc, aux, partial, status, mask);
+    wilson_f32_kernel<R, TPB, true, EPI_NONE, false><<<grid, TPB, 0, s>>>(m.links, in, nullptr, out, g, kap, mu, nrhs, sc, aux, partial, status, mask, m.sites);
   else
-    wilson_f32_kernel<R, TPB, false, EPI_NONE, false><<<grid, TPB, 0, s>>>(m.links, in, nullptr, out, g, kap, mu, nrhs, sc, aux, partial, status, mask);
+    wilson_f32_kernel<R, TPB, false, EPI_NONE, false><<<grid, TPB, 0, s>>>(m.links, in, nullptr, out, g, kap, mu, nrhs, sc, aux, partial, status, mask, m.sites);
   return cudaGetLastError();
 }
 
@@ -286,10 +302,12 @@ cudaError_t launch_wilson_f32(const Mixed32 &m, const float4 *in, const float4 *
                               int nrhs, int dagger, int epi, const BicgScalars *sc,
                               const float4 *aux, double *partial, const int *status,
                               unsigned mask, cudaStream_t s) {
-  ProfLaunch prof(PC_DSLASH, s);
+  ProfLaunch prof(PC_DSLASH_LOW, s);
   int R, T;
   wilson32_shape(m.h, nrhs, &R, &T);
-  return launch_wilson_f32_shape(m, R, T, in, in2, out, nrhs, dagger, epi, sc, aux, partial, status,
+  Mixed32 mc = m;
+  mc.sites = prof_site_counter_low();
+  return launch_wilson_f32_shape(mc, R, T, in, in2, out, nrhs, dagger, epi, sc, aux, partial, status,
                                  mask, s);
 }
 
@@ -578,7 +596,7 @@ int stream32_blocks(long long n4) {
 cudaError_t launch_bicg32_update_p(float4 *p, const float4 *r, const float4 *v,
                                    const BicgScalars *sc, const int *status, long long n4,
                                    int nrhs, cudaStream_t s) {
-  ProfLaunch prof(PC_STREAM, s);
+  ProfLaunch prof(PC_STREAM_LOW, s);
   bicg32_update_p_kernel<<<dim3(stream32_blocks(n4), nrhs), 256, 0, s>>>(p, r, v, sc, status, n4);
   return cudaGetLastError();
 }
@@ -587,7 +605,7 @@ cudaError_t launch_bicg32_update_xr(float4 *xs, float4 *r, const float4 *p, cons
                                     const float4 *t, const float4 *rhat, const BicgScalars *sc,
                                     const int *status, double *partial, long long n4, int nrhs,
                                     cudaStream_t s) {
-  ProfLaunch prof(PC_STREAM, s);
+  ProfLaunch prof(PC_STREAM_LOW, s);
   bicg32_update_xr_kernel<<<dim3(stream32_blocks(n4), nrhs), 256, 0, s>>>(xs, r, p, v, t, rhat, sc,
                                                                          status, partial, n4);
   return cudaGetLastError();

@@ -11,6 +11,7 @@ namespace wd {
 struct Mixed32 {
   const wd_context *h;
   const float4 *links;  // [mu][3][V] float4, rows 0 and 1 of every link
+  unsigned long long *sites = nullptr;  // profiler's work counter (or nullptr)
 };
 
 // launch shape (right-hand sides per thread, threads per block) and grid

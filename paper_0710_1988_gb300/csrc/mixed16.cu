@@ -178,8 +178,16 @@ __global__ void __launch_bounds__(TPB)
 wilson_f16_kernel(const uint2 *__restrict__ links, Half16 in, const float4 *__restrict__ r32,
                   Half16 out, LatticeGeom g, float kappa, float mu, int nrhs,
                   const BicgScalars *__restrict__ sc, const float4 *__restrict__ aux,
-                  double *__restrict__ partial, const int *__restrict__ status, unsigned mask) {
-  const int r0 = blockIdx.y * R;
+                  double *__restrict__ partial, const int *__restrict__ status, unsigned mask,
+                  unsigned long long *__restrict__ sites) {
+  // Blocks are numbered system-row fastest: the nrow blocks that cover the
+  // same sites run next to each other and share the links and the
+  // neighbour spinors' cache lines through L2.
+  const int nrow = (nrhs + R - 1) / R;
+  const int row = (int)(blockIdx.x % (unsigned)nrow);
+  const long long sb = blockIdx.x / (unsigned)nrow;   // site block
+  const long long nsb = (g.V + TPB - 1) / TPB;        // site blocks
+  const int r0 = row * R;
   const long long V = g.V;
   bool on[R];
   bool any = false;
@@ -189,11 +197,17 @@ wilson_f16_kernel(const uint2 *__restrict__ links, Half16 in, const float4 *__re
     any |= on[r];
   }
   if (!any) return;
+  if (sites != nullptr && sb == 0 && threadIdx.x == 0) {
+    int cnt = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) cnt += on[r] ? 1 : 0;
+    atomicAdd(sites, (unsigned long long)V * cnt);  // work accounting for the profiler
+  }
   float2 alpha[R];
 #pragma unroll
   for (int r = 0; r < R; ++r)
     alpha[r] = (FUSED && on[r]) ? f2of(sc[r0 + r].alpha) : make_float2(0.f, 0.f);
-  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long s = sb * TPB + threadIdx.x;
   float red[R][3];
 #pragma unroll
   for (int r = 0; r < R; ++r) red[r][0] = red[r][1] = red[r][2] = 0.f;
@@ -274,7 +288,7 @@ wilson_f16_kernel(const uint2 *__restrict__ links, Half16 in, const float4 *__re
         double t = 0.0;
 #pragma unroll
         for (int w2 = 0; w2 < NW; ++w2) t += sh[r][q][w2];
-        partial[((long long)(r0 + r) * gridDim.x + blockIdx.x) * 3 + q] = t;
+        partial[((long long)(r0 + r) * nsb + sb) * 3 + q] = t;
       }
     }
   }
@@ -284,18 +298,20 @@ template <int R, int TPB>
 static cudaError_t launch_w16(const wd_context *h, const uint2 *links, Half16 in, const float4 *r32,
                               Half16 out, int nrhs, int dagger, int epi, const BicgScalars *sc,
                               const float4 *aux, double *partial, const int *status,
-                              unsigned mask, cudaStream_t s) {
+                              unsigned mask, unsigned long long *sites, cudaStream_t s) {
   const LatticeGeom g = geom_of(h);
-  dim3 grid((unsigned)((h->V + TPB - 1) / TPB), (nrhs + R - 1) / R);
+  const long long nblk = (h->V + TPB - 1) / TPB * ((nrhs + R - 1) / R);
+  if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  const dim3 grid((unsigned)nblk);
   const float kap = (float)h->kappa, mu = (float)h->mu;
   if (epi == EPI_DOT)
-    wilson_f16_kernel<R, TPB, false, EPI_DOT, false><<<grid, TPB, 0, s>>>(links, in, r32, out, g, kap, mu, nrhs, sc, aux, partial, status, mask);
+    wilson_f16_kernel<R, TPB, false, EPI_DOT, false><<<grid, TPB, 0, s>>>(links, in, r32, out, g, kap, mu, nrhs, sc, aux, partial, status, mask, sites);
   else if (epi == EPI_TSTT)
-    wilson_f16_kernel<R, TPB, false, EPI_TSTT, true><<<grid, TPB, 0, s>>>(links, in, r32, out, g, kap, mu, nrhs, sc, aux, partial, status, mask);
+    wilson_f16_kernel<R, TPB, false, EPI_TSTT, true><<<grid, TPB, 0, s>>>(links, in, r32, out, g, kap, mu, nrhs, sc, aux, partial, status, mask, sites);
   else if (dagger)
-    wilson_f16_kernel<R, TPB, true, EPI_NONE, false><<<grid, TPB, 0, s>>>(links, in, r32, out, g, kap, mu, nrhs, sc, aux, partial, status, mask);
+    wilson_f16_kernel<R, TPB, true, EPI_NONE, false><<<grid, TPB, 0, s>>>(links, in, r32, out, g, kap, mu, nrhs, sc, aux, partial, status, mask, sites);
   else
-    wilson_f16_kernel<R, TPB, false, EPI_NONE, false><<<grid, TPB, 0, s>>>(links, in, r32, out, g, kap, mu, nrhs, sc, aux, partial, status, mask);
+    wilson_f16_kernel<R, TPB, false, EPI_NONE, false><<<grid, TPB, 0, s>>>(links, in, r32, out, g, kap, mu, nrhs, sc, aux, partial, status, mask, sites);
   return cudaGetLastError();
 }
 
@@ -324,11 +340,11 @@ static cudaError_t launch_w16_shape(const wd_context *h, int R, int T, const uin
                                     Half16 in, const float4 *r32, Half16 out, int nrhs, int dagger,
                                     int epi, const BicgScalars *sc, const float4 *aux,
                                     double *partial, const int *status, unsigned mask,
-                                    cudaStream_t s) {
+                                    unsigned long long *sites, cudaStream_t s) {
 #define W16(RR, TT)                                                                           \
   if (R == RR && T == TT)                                                                     \
     return launch_w16<RR, TT>(h, links, in, r32, out, nrhs, dagger, epi, sc, aux, partial, \
-                              status, mask, s);
+                              status, mask, sites, s);
   W16(1, 64) W16(1, 128) W16(1, 256)
   W16(2, 64) W16(2, 128) W16(2, 256)
   W16(4, 64) W16(4, 128) W16(4, 256)
@@ -340,11 +356,11 @@ cudaError_t launch_wilson_f16(const wd_context *h, const uint2 *links, Half16 in
                               Half16 out, int nrhs, int dagger, int epi, const BicgScalars *sc,
                               const float4 *aux, double *partial, const int *status,
                               unsigned mask, cudaStream_t s) {
-  ProfLaunch prof(PC_DSLASH, s);
+  ProfLaunch prof(PC_DSLASH_LOW, s);
   int R, T;
   wilson16_shape(h, nrhs, &R, &T);
   return launch_w16_shape(h, R, T, links, in, r32, out, nrhs, dagger, epi, sc, aux, partial,
-                          status, mask, s);
+                          status, mask, prof_site_counter_low(), s);
 }
 
 // Times every launch shape on (in -> out) and keeps the fastest for nrhs.
@@ -362,12 +378,12 @@ cudaError_t tune_wilson_f16(wd_context *h, const uint2 *links, int nrhs, Half16 
     for (int T : Ts) {
       for (int w = 0; w < 2 && err == cudaSuccess; ++w)
         err = launch_w16_shape(h, R, T, links, in, nullptr, out, nrhs, 0, EPI_NONE, nullptr,
-                               nullptr, nullptr, nullptr, M_ALL, s);
+                               nullptr, nullptr, nullptr, M_ALL, nullptr, s);
       float t_best = 1e30f;
       for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
         cudaEventRecord(e0, s);
         err = launch_w16_shape(h, R, T, links, in, nullptr, out, nrhs, 0, EPI_NONE, nullptr,
-                               nullptr, nullptr, nullptr, M_ALL, s);
+                               nullptr, nullptr, nullptr, M_ALL, nullptr, s);
         cudaEventRecord(e1, s);
         cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -562,7 +578,7 @@ int stream16_blocks(long long V) { return (int)site_blocks(V); }
 
 cudaError_t launch_bicg16_update_p(Half16 p, const float4 *r, Half16 v, const BicgScalars *sc,
                                    const int *status, long long V, int nrhs, cudaStream_t s) {
-  ProfLaunch prof(PC_STREAM, s);
+  ProfLaunch prof(PC_STREAM_LOW, s);
   bicg16_update_p_kernel<<<dim3(site_blocks(V), nrhs), 256, 0, s>>>(p, r, v, sc, status, V);
   return cudaGetLastError();
 }
@@ -570,7 +586,7 @@ cudaError_t launch_bicg16_update_p(Half16 p, const float4 *r, Half16 v, const Bi
 cudaError_t launch_bicg16_update_xr(float4 *xs, float4 *r, Half16 p, Half16 v, Half16 t,
                                     const float4 *rhat, const BicgScalars *sc, const int *status,
                                     double *partial, long long V, int nrhs, cudaStream_t s) {
-  ProfLaunch prof(PC_STREAM, s);
+  ProfLaunch prof(PC_STREAM_LOW, s);
   bicg16_update_xr_kernel<<<dim3(site_blocks(V), nrhs), 256, 0, s>>>(xs, r, p, v, t, rhat, sc,
                                                                      status, partial, V);
   return cudaGetLastError();

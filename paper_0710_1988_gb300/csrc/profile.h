@@ -15,7 +15,10 @@
 
 namespace wd {
 
-enum ProfCat { PC_DSLASH = 0, PC_STREAM = 1, PC_TS = 2, PC_DENSE = 3, PC_COUNT = 4 };
+enum ProfCat {
+  PC_DSLASH = 0, PC_STREAM = 1, PC_TS = 2, PC_DENSE = 3, PC_DSLASH_LOW = 4, PC_STREAM_LOW = 5,
+  PC_COUNT = 6
+};
 
 struct Profiler {
   unsigned mask = 0;              // categories being recorded
@@ -25,9 +28,11 @@ struct Profiler {
   };
   std::vector<Rec> pending;
   std::vector<cudaEvent_t> spare;
-  long long launches[PC_COUNT] = {0, 0, 0, 0};
-  double ms[PC_COUNT] = {0, 0, 0, 0};
-  unsigned long long *d_sites = nullptr;  // device counter: sites x systems processed by dslash
+  long long launches[PC_COUNT] = {0, 0, 0, 0, 0, 0};
+  double ms[PC_COUNT] = {0, 0, 0, 0, 0, 0};
+  // device counters of sites x systems processed: [0] FP64 dslash,
+  // [1] FP32/FP16 dslash
+  unsigned long long *d_sites = nullptr;
   cudaEvent_t take();
   void flush();                   // synchronises the pending events and accumulates
   void reset();
@@ -65,10 +70,14 @@ struct ProfLaunch {
   }
 };
 
-// Device counter of dslash work (nullptr unless dslash profiling is on).
+// Device counters of dslash work (nullptr unless that category is profiled).
 inline unsigned long long *prof_site_counter() {
   Profiler *q = current_profiler();
-  return (q != nullptr && (q->mask & 1u)) ? q->d_sites : nullptr;
+  return (q != nullptr && ((q->mask >> PC_DSLASH) & 1u)) ? q->d_sites : nullptr;
+}
+inline unsigned long long *prof_site_counter_low() {
+  Profiler *q = current_profiler();
+  return (q != nullptr && ((q->mask >> PC_DSLASH_LOW) & 1u)) ? q->d_sites + 1 : nullptr;
 }
 
 }  // namespace wd

@@ -1,0 +1,55 @@
+"""Run one Wilson-operator kernel on its own, for profilers and timing.
+
+    python -m paper_0710_1988_gb300.kernel_case --kernel f32 --lattice 20 20 20 32 --nrhs 12
+
+Builds a seeded gauge field (U = exp(i 0.5 H)) and Gaussian spinors, then
+applies the operator `--reps` times through the public binding (`apply`,
+`apply_f32` or `apply_f16`) and prints the mean time per application from
+the handle's own kernel timing.  The low-precision entry points also run
+their conversion kernels; a profiler selects the Wilson kernel by name.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+
+
+def main(argv=None):
+    import torch
+
+    import paper_0710_1988_gb300 as wdl
+    from inputs import lattice as L
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--kernel", choices=["f64", "f32", "f16"], default="f32")
+    ap.add_argument("--lattice", type=int, nargs=4, default=[20, 20, 20, 32])
+    ap.add_argument("--nrhs", type=int, default=12)
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--kappa", type=float, default=0.14)
+    args = ap.parse_args(argv)
+    dims = tuple(args.lattice)
+    U = L.gauge_field(dims, 0.5, 1002)
+    psi = L.gaussian_spinor(dims, 2200, nrhs=args.nrhs).reshape(-1)
+    op = wdl.WilsonOperator(dims, torch.from_numpy(U).cuda(), args.kappa)
+    x = torch.from_numpy(psi).cuda()
+    y = torch.empty_like(x)
+    fn = {"f64": op.apply, "f32": op.apply_f32, "f16": op.apply_f16}[args.kernel]
+    fn(x, y)
+    torch.cuda.synchronize()
+    op.profile(mask=0x11)
+    for _ in range(args.reps):
+        fn(x, y)
+    torch.cuda.synchronize()
+    p = op.profile_read()
+    op.profile(mask=0)
+    cat = "dslash" if args.kernel == "f64" else "dslash_low"
+    ms = p[cat]["ms"] / max(1, p[cat]["launches"])
+    print(json.dumps({"kernel": args.kernel, "lattice": list(dims), "nrhs": args.nrhs,
+                      "ms_per_apply": ms, "finite": bool(np.isfinite(y.abs().max().item()))}))
+    op.close()
+
+
+if __name__ == "__main__":
+    main()
