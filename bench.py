@@ -46,9 +46,9 @@ SM_MAX_MHZ = 2070.0
 DSLASH_FLOPS_PER_SITE = 1368      # 1320 hopping + 48 for 1 - kappa*D
 DSLASH_BYTES_PER_SITE = 960       # 192 in + 192 out + 4 links x 144 (FP64)
 # DRAM bytes (read + write) per site update of wilson_f64_kernel from one ncu
-# capture of a 10-system launch at 16^4 (497.6 MB / 655,360 site updates);
-# the bench scales it to a launch by the site updates the launch processed.
-DSLASH_DRAM_BYTES_PER_SITE_UPDATE = 497.6e6 / 655360
+# capture of a 10-system launch at 16^4 (383.6 + 111.4 MB / 655,360 site
+# updates); the bench scales it to a launch by the site updates it processed.
+DSLASH_DRAM_BYTES_PER_SITE_UPDATE = 495.0e6 / 655360
 METRIC = "D-BiCGStab solves/s at rel. residual 1e-10; dslash GB/s vs HBM roofline"
 
 
@@ -64,6 +64,12 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--storage", type=int, default=32, choices=[32, 16],
                     help="Krylov vector storage of the mixed workloads")
+    ap.add_argument("--mixed-delta", type=float, default=None,
+                    help="mixed solver: 0 = reliable updates every 50 iterations, delta in "
+                         "(0, 1) = restarted refinement (default: 0 for the mixed Wilson "
+                         "workload, 1e-3 for the twisted-mass shifts)")
+    ap.add_argument("--mus", type=float, nargs="*", default=None,
+                    help="twisted-mass shifts (default: the preset's)")
     return ap.parse_args()
 
 
@@ -413,7 +419,7 @@ def roofline(res, peaks, fp64_peak):
         "peak_source": fp64_peak["source"],
         "traffic": round(DSLASH_DRAM_BYTES_PER_SITE_UPDATE * sites_per_launch),
         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 16^4 "
-                          "10-system launch (759 B per site update), scaled to the average "
+                          "10-system launch (755 B per site update), scaled to the average "
                           "launch by site updates",
         "algorithmic_flops_per_launch": flops,
         "avg_launch_ms": avg_ms,
@@ -626,6 +632,8 @@ def mixed_arm(args, cfg, rank, world, local_rank):
     V = torch.zeros(cfg.k * n, dtype=torch.complex128, device=dev)
     op = wdl.WilsonOperator(cfg.dims, torch.from_numpy(U).to(dev), kappa)
     op.set_mixed_storage(args.storage)
+    delta = 0.0 if args.mixed_delta is None else args.mixed_delta
+    op.set_mixed_restart(delta, 4000)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -653,9 +661,11 @@ def mixed_arm(args, cfg, rank, world, local_rank):
     # D-BiCGStab alone: FP64 against FP32 and FP16 storage, same V and sources
     defl = op.deflation(V, cfg.k)
     comp = {}
-    for name, bits in (("fp64", None), ("mixed32", 32), ("mixed16", 16)):
+    for name, bits, dl in (("fp64", None, 0.0), ("mixed32", 32, 0.0), ("mixed16", 16, 0.0),
+                           ("mixed32_restarted", 32, 1e-3), ("mixed16_restarted", 16, 1e-3)):
         if bits:
             op.set_mixed_storage(bits)
+            op.set_mixed_restart(dl, 4000)
         fn = op.dbicgstab if bits is None else (
             lambda B_, X_, d_, tol: op.dbicgstab_mixed(B_, X_, d_, tol=tol, reliable_every=50))
         X.zero_()
@@ -674,8 +684,12 @@ def mixed_arm(args, cfg, rank, world, local_rank):
                       "max_true_rel_res": max(q["true_rel_res"] for q in ss)}
     defl.close()
     op.set_mixed_storage(args.storage)
-    for name in ("mixed32", "mixed16"):
-        comp[name]["speedup_vs_fp64"] = round(comp[name]["solves_per_s"] / comp["fp64"]["solves_per_s"], 3)
+    op.set_mixed_restart(delta, 4000)
+    for name in comp:
+        if name != "fp64":
+            comp[name]["speedup_vs_fp64"] = round(comp[name]["solves_per_s"] / comp["fp64"]["solves_per_s"], 3)
+    comp["strategies"] = {"mixed32/16": "reliable updates every 50 iterations",
+                          "*_restarted": "restarted refinement, delta = 1e-3"}
     op.close()
     extra = {
         "gpu_launches": None,
@@ -693,7 +707,9 @@ def mixed_arm(args, cfg, rank, world, local_rank):
     return _row_line(cfg, args, world, cfg.n_rhs * args.steps * world / (total_ms * 1e-3),
                      "solves/s", total_ms, f"f{args.storage} iteration, f64 reliable updates",
                      f"{cfg.name}: GMRES-DR({cfg.m},{cfg.k}) FP64 on 1 Z4 source + D-BiCGStab("
-                     f"{cfg.k}) mixed (FP{args.storage} storage, FP64 reliable updates every 50) "
+                     f"{cfg.k}) mixed (FP{args.storage} storage, "
+                     + ("FP64 reliable updates every 50" if delta == 0 else
+                        f"restarted refinement delta {delta:g}") + ") "
                      f"on {cfg.n_rhs} Z4 sources, tol {cfg.tol:g}, kappa = {cfg.kappa_factor} kappa_c",
                      extra)
 
@@ -710,11 +726,13 @@ def twisted_arm(args, cfg, rank, world, local_rank):
     U = L.gauge_field(cfg.dims, cfg.eps, L.link_seed(cfg))
     v = L.volume(cfg.dims)
     n = 12 * v
-    mus = sorted(cfg.mus, reverse=True)
+    mus = sorted(args.mus if args.mus else cfg.mus, reverse=True)
     B = torch.from_numpy(rank_sources(cfg, rank, cfg.n_rhs).reshape(cfg.n_rhs, n)).to(dev)
     X = torch.zeros(len(mus) * cfg.n_rhs * n, dtype=torch.complex128, device=dev)
     op = wdl.WilsonOperator(cfg.dims, torch.from_numpy(U).to(dev), kappa)
     op.set_mixed_storage(args.storage)
+    delta = 1e-3 if args.mixed_delta is None else args.mixed_delta
+    op.set_mixed_restart(delta, 4000)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -762,8 +780,10 @@ def twisted_arm(args, cfg, rank, world, local_rank):
                      total_ms, f"f{args.storage} iteration, f64 reliable updates",
                      f"{cfg.name}: A_W + i mu gamma5 at kappa_c, shifts {mus} heaviest first, each "
                      f"projected over the earlier solutions (Sec. 4), {cfg.n_rhs} Gaussian sources "
-                     f"per shift batched, mixed BiCGStab to {cfg.tol:g}; value counts (source, shift) "
-                     f"pairs", extra)
+                     f"per shift batched, mixed BiCGStab (FP{args.storage}, "
+                     + ("reliable updates every 50" if delta == 0 else
+                        f"restarted refinement delta {delta:g}")
+                     + f") to {cfg.tol:g}; value counts (source, shift) pairs", extra)
 
 
 def grad_arm(args, cfg, rank, world, local_rank):

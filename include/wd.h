@@ -230,10 +230,26 @@ int wd_apply_f32(wd_handle h, const void *in, void *out, int nrhs, int dagger,
  * the handle (nrhs >= 33 share one slot).  The mixed solver runs it on
  * first use of an nrhs; R, threads, ms (NULL or host) report the choice.
  * wd_set_f32_shape fixes a shape by hand (R = threads = 0: back to the
- * default R by nrhs, 128 threads). */
+ * default, R = 1 and 128 threads). */
 int wd_autotune_f32(wd_handle h, int nrhs, int *R, int *threads, float *ms,
                     wd_stream stream);
 int wd_set_f32_shape(wd_handle h, int nrhs, int R, int threads);
+
+/* Strategy of the mixed solver (not in the paper).  delta = 0 (default):
+ * reliable updates -- every reliable_every iterations, and whenever the
+ * low-precision recursive residual reaches tol, x and r = b - A x are
+ * refreshed in FP64 and the BiCGStab recurrence continues with the replaced
+ * residual.  0 < delta < 1: restarted refinement -- the low-precision
+ * BiCGStab runs until its recursive residual has fallen by delta (or
+ * max_inner iterations pass), then the FP64 residual is recomputed and the
+ * recurrence restarts from it (r_hat = r, p = v = 0).  Reliable updates keep
+ * the Krylov space and are fastest on well-conditioned systems; restarted
+ * refinement converges where the low-precision recurrence loses too much
+ * accuracy (e.g. twisted mass near kappa_c).  Applies to
+ * dbicgstab_solve_mixed and tm_multishift_solve with mixed = 1; wd_stats
+ * .restarts counts the restarts.  WD_BAD_ARG for delta outside [0, 1) or
+ * max_inner < 1 with delta > 0. */
+int wd_set_mixed_restart(wd_handle h, double delta, int max_inner);
 
 /* Storage of the mixed solver's iteration (not in the paper): bits = 32
  * (default) keeps every Krylov vector in FP32; bits = 16 stores the links

@@ -69,6 +69,25 @@ def link_force(links, dims, kappa, lam, x):
     return out.reshape(v, 4, 8)
 
 
+def link_force_at(links, dims, kappa, lam, x, pairs):
+    """dL/domega_{s,mu,a} for a few (s, mu) pairs, shape (len(pairs), 8): the
+    same formula as `link_force`, walked site by site through explicit
+    coordinates, so that a full-size result can be checked one link at a time."""
+    out = np.zeros((len(pairs), 8))
+    for i, (s, mu) in enumerate(pairs):
+        c = list(dirac.site_coords(dims, int(s)))
+        c[mu] += 1
+        sp = dirac.site_index(dims, *c)
+        u = links[s, mu]
+        phi = (dirac.ONE4 - dirac.GAMMA[mu]) @ x[sp]          # spin x colour
+        psi = (dirac.ONE4 + dirac.GAMMA[mu]) @ x[s]
+        o1 = phi.T @ np.conj(lam[s])                          # sum over spin
+        o2 = psi.T @ np.conj(lam[sp])
+        m = u @ o1 - o2 @ np.conj(u.T)
+        out[i] = -kappa * np.array([np.trace(T[a] @ m).imag for a in range(8)])
+    return out
+
+
 def gradients(links, dims, kappa, b, eta, solve, solve_dagger, mu: float = 0.0):
     """(L, dL/db, dL/dkappa, dL/domega) for L = Re(eta^dagger A^{-1} b).
 

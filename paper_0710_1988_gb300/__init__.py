@@ -254,6 +254,12 @@ class WilsonOperator:
     def set_f16_shape(self, nrhs: int, R: int, threads: int):
         check(lib().wd_set_f16_shape(self._h, int(nrhs), int(R), int(threads)))
 
+    def set_mixed_restart(self, delta: float, max_inner: int = 2000):
+        """Mixed solver strategy: delta = 0 reliable updates (default); delta
+        in (0, 1) restarted refinement, each low-precision pass reducing the
+        residual by delta (at most max_inner iterations)."""
+        check(lib().wd_set_mixed_restart(self._h, float(delta), int(max_inner)))
+
     def set_mixed_storage(self, bits: int):
         """Storage of the mixed solver's Krylov vectors: 32 (default) or 16."""
         check(lib().wd_set_mixed_storage(self._h, int(bits)))

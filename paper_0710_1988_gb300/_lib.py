@@ -82,6 +82,7 @@ SIGNATURES = {
     "wd_autotune_f32": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float), P]),
     "wd_set_f32_shape": (I, [P, I, I, I]),
     "wd_set_mixed_storage": (I, [P, I]),
+    "wd_set_mixed_restart": (I, [P, D, I]),
     "wd_apply_f16": (I, [P, P, P, I, I, P]),
     "wd_autotune_f16": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float), P]),
     "wd_set_f16_shape": (I, [P, I, I, I]),

@@ -134,6 +134,8 @@ extern "C" int wd_create(const int lat[4], const void *links, double kappa, doub
   h->links32 = nullptr;
   h->links16 = nullptr;
   h->mixed_bits = 32;
+  h->mixed_delta = 0.0;
+  h->mixed_inner_max = 2000;
   h->side = nullptr;
   h->ev_in = h->ev_out = nullptr;
   h->eo = 0;
@@ -781,6 +783,15 @@ extern "C" int wd_set_f16_shape(wd_handle h, int nrhs, int R, int threads) {
   h->tune16_R[key] = R;
   h->tune16_T[key] = threads;
   h->tune16_ms[key] = 0.f;
+  return WD_OK;
+}
+
+extern "C" int wd_set_mixed_restart(wd_handle h, double delta, int max_inner) {
+  if (h == nullptr) return bad("wd_set_mixed_restart: NULL handle");
+  if (!(delta >= 0.0 && delta < 1.0)) return bad("wd_set_mixed_restart: delta must be in [0, 1)");
+  if (delta > 0.0 && max_inner < 1) return bad("wd_set_mixed_restart: max_inner must be >= 1");
+  h->mixed_delta = delta;
+  h->mixed_inner_max = delta > 0.0 ? max_inner : h->mixed_inner_max;
   return WD_OK;
 }
 

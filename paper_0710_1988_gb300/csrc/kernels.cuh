@@ -37,6 +37,10 @@ struct BicgScalars {
   double bnorm, rhat_norm, rnorm, true_rel, tol;
   int iters, max_iter, restarts, max_restarts;
   long long mvp, mvp_extra;
+  // mixed solver only: tol is the target of the low-precision recursion;
+  // tol_outer the FP64 true-residual target; delta > 0 selects restarted
+  // refinement (inner target delta x the residual at the last restart)
+  double tol_outer, delta;
 };
 
 LatticeGeom geom_of(const wd_context *h);

@@ -272,8 +272,9 @@ static cudaError_t launch_w32(const Mixed32 &m, const float4 *in, const float4 *
 }
 
 // Launch shape of the FP32 kernel for nrhs right-hand sides: the autotuned
-// (R, threads per block) of the handle when there is one, else R = 4/2/1 by
-// nrhs and 128 threads.
+// (R, threads per block) of the handle when there is one, else R = 1 and 128
+// threads (the tuner's choice on 16^4 and 20^3 x 32 for 1 to 12 systems:
+// R > 1 saves link loads from L2 but its registers cost more occupancy).
 void wilson32_shape(const wd_context *h, int nrhs, int *R, int *T) {
   const int key = nrhs < WD_TUNE_SLOTS ? nrhs : WD_TUNE_SLOTS - 1;
   if (h->tune_R[key] > 0) {
@@ -281,7 +282,7 @@ void wilson32_shape(const wd_context *h, int nrhs, int *R, int *T) {
     *T = h->tune_T[key];
     return;
   }
-  *R = nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1);
+  *R = 1;
   *T = 128;
 }
 
@@ -622,8 +623,13 @@ cudaError_t launch_bicg32_restart(float4 *rhat, const float4 *r, float4 *p, floa
 
 // ----------------------------------------------------------------- reliable update finalizer
 // partial (NQ = 3): <rhat32, r32>, (unused), ||r64||^2 from f64_to_f32_kernel.
+// A system is done when its FP64 residual meets tol_outer.  Otherwise, with
+// restarted refinement (delta > 0), a system whose recursion reached its
+// inner target, or every system when `force` is set, restarts the recurrence
+// from the FP64 residual with the next inner target; the others continue
+// with the replaced residual (reliable update).
 __global__ void reliable_finalize_kernel(const double *__restrict__ partial, int nb,
-                                         BicgScalars *sc, int *status, unsigned mask) {
+                                         BicgScalars *sc, int *status, unsigned mask, int force) {
   const int r = blockIdx.x;
   const int st = status[r];
   if (!((mask >> st) & 1u)) return;
@@ -642,17 +648,40 @@ __global__ void reliable_finalize_kernel(const double *__restrict__ partial, int
   S.true_rel = S.rnorm / S.bnorm;
   S.rho = make_double2(v[0], v[1]);  // <rhat, r> with the replaced residual
   if (st == ST_BREAKDOWN || st == ST_MAXITER) return;  // final: record only
-  if (S.true_rel <= S.tol) {
+  if (S.true_rel <= S.tol_outer) {
     status[r] = ST_DONE;
+  } else if (S.delta > 0.0 && (st == ST_RECURSIVE || force)) {
+    S.tol = fmax(S.tol_outer, S.delta * S.true_rel);
+    S.rho = make_double2(v[2], 0.0);  // r_hat = r after the restart
+    S.rho_old = make_double2(1.0, 0.0);
+    S.alpha = make_double2(1.0, 0.0);
+    S.omega = make_double2(1.0, 0.0);
+    S.rhat_norm = S.rnorm;
+    S.restarts += 1;
+    status[r] = ST_RESTART;
   } else {
     status[r] = ST_ACTIVE;
   }
 }
 
 cudaError_t launch_reliable_finalize(const double *partial, int nb, BicgScalars *sc, int *status,
-                                     unsigned mask, int nrhs, cudaStream_t s) {
+                                     unsigned mask, int nrhs, cudaStream_t s, int force) {
   ProfLaunch prof(PC_STREAM, s);
-  reliable_finalize_kernel<<<nrhs, 256, 0, s>>>(partial, nb, sc, status, mask);
+  reliable_finalize_kernel<<<nrhs, 256, 0, s>>>(partial, nb, sc, status, mask, force);
+  return cudaGetLastError();
+}
+
+// First inner target of restarted refinement: delta x the initial residual.
+__global__ void mixed_inner_tol_kernel(BicgScalars *sc, const int *status, int nrhs) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs || status[r] != ST_ACTIVE) return;
+  BicgScalars &S = sc[r];
+  if (S.delta > 0.0) S.tol = fmax(S.tol_outer, S.delta * S.rnorm / S.bnorm);
+}
+
+cudaError_t launch_mixed_inner_tol(BicgScalars *sc, const int *status, int nrhs, cudaStream_t s) {
+  ProfLaunch prof(PC_STREAM, s);
+  mixed_inner_tol_kernel<<<(nrhs + 127) / 128, 128, 0, s>>>(sc, status, nrhs);
   return cudaGetLastError();
 }
 

@@ -79,6 +79,7 @@ cudaError_t launch_bicg16_restart(float4 *rhat, const float4 *r, Half16 p, Half1
                                   cudaStream_t s);
 
 cudaError_t launch_reliable_finalize(const double *partial, int nb, BicgScalars *sc, int *status,
-                                     unsigned mask, int nrhs, cudaStream_t s);
+                                     unsigned mask, int nrhs, cudaStream_t s, int force = 0);
+cudaError_t launch_mixed_inner_tol(BicgScalars *sc, const int *status, int nrhs, cudaStream_t s);
 
 }  // namespace wd

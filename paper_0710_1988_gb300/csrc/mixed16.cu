@@ -317,8 +317,8 @@ static cudaError_t launch_w16(const wd_context *h, const uint2 *links, Half16 in
 
 static int tune_key16(int nrhs) { return nrhs < WD_TUNE_SLOTS ? nrhs : WD_TUNE_SLOTS - 1; }
 
-// Launch shape for nrhs systems: the tuned one if any, else R = 2 (1 for a
-// single system) right-hand sides per thread and 128 threads per block.
+// Launch shape for nrhs systems: the tuned one if any, else one right-hand
+// side per thread and 128 threads per block.
 void wilson16_shape(const wd_context *h, int nrhs, int *R, int *T) {
   const int key = tune_key16(nrhs);
   if (h->tune16_R[key] != 0) {
@@ -326,7 +326,7 @@ void wilson16_shape(const wd_context *h, int nrhs, int *R, int *T) {
     *T = h->tune16_T[key];
     return;
   }
-  *R = nrhs >= 2 ? 2 : 1;
+  *R = 1;
   *T = 128;
 }
 

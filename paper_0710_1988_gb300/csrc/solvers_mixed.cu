@@ -114,9 +114,12 @@ int bicgstab_mixed_batched(wd_context *h, const double2 *B, double2 *X, const do
   const Mixed32 m{h, h->links32};
 
   std::vector<BicgScalars> hsc(nrhs);
+  const bool restart = h->mixed_delta > 0.0;
   for (auto &q : hsc) {
     std::memset(&q, 0, sizeof(q));
     q.tol = tol;
+    q.tol_outer = tol;
+    q.delta = h->mixed_delta;
     q.max_iter = max_iter;
     q.max_restarts = 0;
   }
@@ -137,7 +140,11 @@ int bicgstab_mixed_batched(wd_context *h, const double2 *B, double2 *X, const do
   RET_IF(ok(launch_f64_to_f32(r64, r, V, nrhs, rhat, part_c, status, M_RECURSIVE, s), "to_f32"));
   RET_IF(ok(launch_reliable_finalize(part_c, nbc, sc, status, M_RECURSIVE, nrhs, s), "reliable0"));
   RET_IF(ok(launch_bicg_finalize(FIN_ACTIVATE, nullptr, 0, sc, status, nullptr, 0, nrhs, s), "activate"));
+  if (restart) RET_IF(ok(launch_mixed_inner_tol(sc, status, nrhs, s), "inner_tol"));
 
+  // restarted refinement checks every `reliable_every` iterations whether a
+  // system reached its inner target and forces a restart after mixed_inner_max
+  const int every = restart ? h->mixed_inner_max : reliable_every;
   const int chunk = reliable_every < 10 ? (reliable_every < 1 ? 1 : reliable_every) : 10;
   auto enqueue_chunk = [&]() -> int {
     for (int it = 0; it < chunk; ++it) {
@@ -196,18 +203,29 @@ int bicgstab_mixed_batched(wd_context *h, const double2 *B, double2 *X, const do
       recursive |= q == ST_RECURSIVE;
     }
     if (!active && !recursive) break;
-    if (recursive || !active || since >= reliable_every) {
+    const bool due = since >= every;
+    if (recursive || !active || due) {
       // reliable update: x += xs, r = b - A x in FP64, r32 = r
       RET_IF(ok(launch_add_f32_to_f64(X, xs, V, nrhs, status, M_RU, s), "x += xs"));
       RET_IF(ok(launch_wilson_f64_epi(h, X, tmp64, nrhs, 0, EPI_NONE, nullptr, nullptr, status, s, M_RU), "w64"));
       RET_IF(ok(launch_sub_norm(r64, B, tmp64, status, M_RU, part_b, n, nrhs, s), "r64"));
       RET_IF(ok(launch_f64_to_f32(r64, r, V, nrhs, rhat, part_c, status, M_RU, s), "r32"));
-      RET_IF(ok(launch_reliable_finalize(part_c, nbc, sc, status, M_RU, nrhs, s), "reliable"));
-      since = 0;
+      RET_IF(ok(launch_reliable_finalize(part_c, nbc, sc, status, M_RU, nrhs, s, restart && due ? 1 : 0), "reliable"));
+      if (!restart || due) since = 0;
       WD_CK(cudaMemcpyAsync(hst.data(), status, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s));
       WD_CK(cudaStreamSynchronize(s));
-      bool left = false;
-      for (int q : hst) left |= q == ST_ACTIVE;
+      bool left = false, restarted = false;
+      for (int q : hst) {
+        left |= q == ST_ACTIVE || q == ST_RESTART;
+        restarted |= q == ST_RESTART;
+      }
+      if (restarted) {  // restarted refinement: r_hat = r, p = v = 0, then active again
+        if (half)
+          RET_IF(ok(launch_bicg16_restart(rhat, r, p16, v16, status, M_RESTART, V, nrhs, s), "restart16"));
+        else
+          RET_IF(ok(launch_bicg32_restart(rhat, r, p, v, status, M_RESTART, n4, nrhs, s), "restart32"));
+        RET_IF(ok(launch_bicg_finalize(FIN_ACTIVATE, nullptr, 0, sc, status, nullptr, 0, nrhs, s), "activate"));
+      }
       if (!left) break;
     }
   }
@@ -230,7 +248,7 @@ int bicgstab_mixed_batched(wd_context *h, const double2 *B, double2 *X, const do
       o.mvp = S.mvp;
       o.mvp_extra += S.mvp_extra;
       o.iters = S.iters;
-      o.restarts = 0;
+      o.restarts = S.restarts;
       o.converged = hst[q] == ST_DONE ? 1 : 0;
       o.breakdown = hst[q] == ST_BREAKDOWN ? 1 : 0;
       o.rel_res = S.bnorm > 0 ? S.rnorm / S.bnorm : 0.0;

@@ -81,6 +81,8 @@ struct wd_context {
   float4 *links32;     // FP32 rows 0, 1 of every link (mixed precision), lazily built
   uint2 *links16;      // FP16 rows 0, 1 of every link, lazily built
   int mixed_bits;      // storage of the mixed solver's Krylov vectors: 32 or 16
+  double mixed_delta;  // 0: reliable updates; > 0: restarted refinement (inner reduction)
+  int mixed_inner_max; // restarted refinement: iterations before a forced restart
   cudaStream_t side;   // non-blocking stream for graph capture when the caller
                        // passes the legacy default stream; lazily created
   cudaEvent_t ev_in, ev_out;

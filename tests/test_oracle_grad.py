@@ -75,3 +75,17 @@ def test_link_force_finite_difference(prob, mu):
     fd1 = (_loss(grad.move_links(U, e, h), kap, b, eta, mu)
            - _loss(grad.move_links(U, e, -h), kap, b, eta, mu)) / (2 * h)
     assert abs(fd1 - f[3, 2, 5]) <= 1e-6 * max(abs(fd1), 1e-3)
+
+
+def test_link_force_at_matches_the_array_form():
+    """The per-link walker used for full-size checks equals the rolled-array
+    form on a lattice with unequal extents (every (s, mu) of it)."""
+    dims = (2, 3, 4, 2)
+    v = L.volume(dims)
+    U = L.gauge_field(dims, 0.7, 91)
+    x = L.gaussian_spinor(dims, 92)
+    lam = L.gaussian_spinor(dims, 93)
+    full = grad.link_force(U, dims, 0.13, lam, x)
+    pairs = [(s, mu) for s in range(v) for mu in range(4)]
+    at = grad.link_force_at(U, dims, 0.13, lam, x, pairs)
+    assert np.abs(at - full.reshape(-1, 8)).max() <= 1e-13 * np.abs(full).max()
