@@ -647,7 +647,7 @@ def mixed_arm(args, cfg, rank, world, local_rank):
     op = wdl.WilsonOperator(cfg.dims, torch.from_numpy(U).to(dev), kappa)
     op.set_mixed_storage(args.storage)
     delta = 0.0 if args.mixed_delta is None else args.mixed_delta
-    op.set_mixed_restart(delta, 4000)
+    op.set_mixed_restart(delta, 300)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -679,7 +679,7 @@ def mixed_arm(args, cfg, rank, world, local_rank):
                            ("mixed32_restarted", 32, 1e-3), ("mixed16_restarted", 16, 1e-3)):
         if bits:
             op.set_mixed_storage(bits)
-            op.set_mixed_restart(dl, 4000)
+            op.set_mixed_restart(dl, 300)
         fn = op.dbicgstab if bits is None else (
             lambda B_, X_, d_, tol: op.dbicgstab_mixed(B_, X_, d_, tol=tol, reliable_every=50))
         X.zero_()
@@ -698,12 +698,12 @@ def mixed_arm(args, cfg, rank, world, local_rank):
                       "max_true_rel_res": max(q["true_rel_res"] for q in ss)}
     defl.close()
     op.set_mixed_storage(args.storage)
-    op.set_mixed_restart(delta, 4000)
+    op.set_mixed_restart(delta, 300)
     for name in comp:
         if name != "fp64":
             comp[name]["speedup_vs_fp64"] = round(comp[name]["solves_per_s"] / comp["fp64"]["solves_per_s"], 3)
     comp["strategies"] = {"mixed32/16": "reliable updates every 50 iterations",
-                          "*_restarted": "restarted refinement, delta = 1e-3"}
+                          "*_restarted": "restarted refinement, delta = 1e-3, a restart at least every 300 iterations"}
     op.close()
     extra = {
         "gpu_launches": None,
@@ -723,7 +723,7 @@ def mixed_arm(args, cfg, rank, world, local_rank):
                      f"{cfg.name}: GMRES-DR({cfg.m},{cfg.k}) FP64 on 1 Z4 source + D-BiCGStab("
                      f"{cfg.k}) mixed (FP{args.storage} storage, "
                      + ("FP64 reliable updates every 50" if delta == 0 else
-                        f"restarted refinement delta {delta:g}") + ") "
+                        f"restarted refinement delta {delta:g}, max 300 iterations per pass") + ") "
                      f"on {cfg.n_rhs} Z4 sources, tol {cfg.tol:g}, kappa = {cfg.kappa_factor} kappa_c",
                      extra)
 
@@ -746,7 +746,7 @@ def twisted_arm(args, cfg, rank, world, local_rank):
     op = wdl.WilsonOperator(cfg.dims, torch.from_numpy(U).to(dev), kappa)
     op.set_mixed_storage(args.storage)
     delta = 1e-3 if args.mixed_delta is None else args.mixed_delta
-    op.set_mixed_restart(delta, 4000)
+    op.set_mixed_restart(delta, 300)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -796,7 +796,7 @@ def twisted_arm(args, cfg, rank, world, local_rank):
                      f"projected over the earlier solutions (Sec. 4), {cfg.n_rhs} Gaussian sources "
                      f"per shift batched, mixed BiCGStab (FP{args.storage}, "
                      + ("reliable updates every 50" if delta == 0 else
-                        f"restarted refinement delta {delta:g}")
+                        f"restarted refinement delta {delta:g}, max 300 iterations per pass")
                      + f") to {cfg.tol:g}; value counts (source, shift) pairs", extra)
 
 

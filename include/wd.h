@@ -241,7 +241,7 @@ int wd_set_f32_shape(wd_handle h, int nrhs, int R, int threads);
  * refreshed in FP64 and the BiCGStab recurrence continues with the replaced
  * residual.  0 < delta < 1: restarted refinement -- the low-precision
  * BiCGStab runs until its recursive residual has fallen by delta (or
- * max_inner iterations pass), then the FP64 residual is recomputed and the
+ * max_inner iterations pass; 300 until set), then the FP64 residual is recomputed and the
  * recurrence restarts from it (r_hat = r, p = v = 0).  Reliable updates keep
  * the Krylov space and are fastest on well-conditioned systems; restarted
  * refinement converges where the low-precision recurrence loses too much

@@ -254,7 +254,7 @@ class WilsonOperator:
     def set_f16_shape(self, nrhs: int, R: int, threads: int):
         check(lib().wd_set_f16_shape(self._h, int(nrhs), int(R), int(threads)))
 
-    def set_mixed_restart(self, delta: float, max_inner: int = 2000):
+    def set_mixed_restart(self, delta: float, max_inner: int = 300):
         """Mixed solver strategy: delta = 0 reliable updates (default); delta
         in (0, 1) restarted refinement, each low-precision pass reducing the
         residual by delta (at most max_inner iterations)."""

@@ -135,7 +135,7 @@ extern "C" int wd_create(const int lat[4], const void *links, double kappa, doub
   h->links16 = nullptr;
   h->mixed_bits = 32;
   h->mixed_delta = 0.0;
-  h->mixed_inner_max = 2000;
+  h->mixed_inner_max = 300;
   h->side = nullptr;
   h->ev_in = h->ev_out = nullptr;
   h->eo = 0;

@@ -38,14 +38,13 @@ bicg_update_p_kernel(double2 *__restrict__ p, const double2 *__restrict__ rv,
   const BicgScalars S = sc[r];
   // beta = (rho / rho_old) (alpha / omega)
   const double2 beta = cmul(cdiv(S.rho, S.rho_old), cdiv(S.alpha, S.omega));
-  const double2 om = S.omega;
+  const double2 mbo = cneg(cmul(beta, S.omega));
   const long long off = (long long)r * n;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const double2 pi = p[off + i], vi = vv[off + i], ri = rv[off + i];
-    // p = r + beta (p - omega v)
-    double2 q = csub(pi, cmul(om, vi));
-    p[off + i] = cfma(beta, q, ri);
+    // p = r + beta (p - omega v) = r + beta p - (beta omega) v: 8 FMA
+    p[off + i] = cfma(mbo, vi, cfma(beta, pi, ri));
   }
 }
 

@@ -203,6 +203,13 @@ LatticeGeom geom_of(const wd_context *h) {
   LatticeGeom g;
   for (int i = 0; i < 4; ++i) g.L[i] = h->dims[i];
   g.V = h->V;
+  for (int i = 0; i < 3; ++i) {
+    const unsigned long long d = (unsigned long long)h->dims[i];
+    int l = 0;
+    while ((1ULL << l) < d) ++l;
+    g.dsh[i] = 31 + l;
+    g.dm[i] = (1ULL << g.dsh[i]) / d + 1;
+  }
   return g;
 }
 

@@ -10,6 +10,12 @@ namespace wd {
 struct LatticeGeom {
   int L[4];
   long long V;
+  // Division by L[0], L[1], L[2] of site indices below 2^31 as a multiply
+  // and a shift (Granlund and Montgomery, "Division by invariant integers
+  // using multiplication", 1994): q = (n * dm) >> dsh with dsh = 31 + l,
+  // l = ceil(log2 d), dm = floor(2^dsh / d) + 1, exact for n < 2^31.
+  unsigned long long dm[3];
+  int dsh[3];
 };
 
 enum { EPI_NONE = 0, EPI_DOT = 1, EPI_TSTT = 2 };

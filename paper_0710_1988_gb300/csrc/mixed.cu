@@ -167,7 +167,7 @@ wilson_f32_kernel(const float4 *__restrict__ links, const float4 *__restrict__ i
   const float4 *inb = in + (long long)r0 * 6 * V;
   const float4 *in2b = FUSED ? in2 + (long long)r0 * 6 * V : nullptr;
   if (s < V) {
-    const Nbrs nb = neighbours(s, g.L);
+    const Nbrs32 nb = neighbours32((unsigned)s, g);
     float2 acc[R][12];
 #pragma unroll
     for (int r = 0; r < R; ++r)

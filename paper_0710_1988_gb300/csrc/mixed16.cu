@@ -212,7 +212,7 @@ wilson_f16_kernel(const uint2 *__restrict__ links, Half16 in, const float4 *__re
 #pragma unroll
   for (int r = 0; r < R; ++r) red[r][0] = red[r][1] = red[r][2] = 0.f;
   if (s < V) {
-    const Nbrs nb = neighbours(s, g.L);
+    const Nbrs32 nb = neighbours32((unsigned)s, g);
     float2 acc[R][12];
 #pragma unroll
     for (int r = 0; r < R; ++r)

@@ -48,6 +48,10 @@ struct GraphGuard {
 }  // namespace
 
 int ensure_links32(wd_context *h, cudaStream_t s) {
+  if (h->V >= (1LL << 31)) {
+    set_error("the FP32/FP16 kernels index sites with 32 bits: fewer than 2^31 sites");
+    return WD_BAD_ARG;
+  }
   if (h->eo) {
     set_error("the FP32 kernels act on the full operator: switch the handle back with wd_set_operator(h, 0)");
     return WD_BAD_ARG;
@@ -59,6 +63,10 @@ int ensure_links32(wd_context *h, cudaStream_t s) {
 }
 
 int ensure_links16(wd_context *h, cudaStream_t s) {
+  if (h->V >= (1LL << 31)) {
+    set_error("the FP32/FP16 kernels index sites with 32 bits: fewer than 2^31 sites");
+    return WD_BAD_ARG;
+  }
   if (h->eo) {
     set_error("the FP16 kernels act on the full operator: switch the handle back with wd_set_operator(h, 0)");
     return WD_BAD_ARG;

@@ -11,6 +11,8 @@
 
 #include <cuda_runtime.h>
 
+#include "kernels.cuh"
+
 namespace wd {
 
 __device__ __forceinline__ double2 sadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -87,6 +89,37 @@ __device__ __forceinline__ Nbrs neighbours(long long s, const int (&L)[4]) {
   nb.dn[2] = z == 0 ? s + (L[2] - 1) * sz : s - sz;
   nb.up[3] = t + 1 == L[3] ? s - (L[3] - 1) * st : s + st;
   nb.dn[3] = t == 0 ? s + (L[3] - 1) * st : s - st;
+  return nb;
+}
+
+// The same for site indices below 2^31 (the FP32 / FP16 kernels), with
+// 32-bit arithmetic and the geometry's multiply-shift divisions.
+struct Nbrs32 {
+  unsigned up[4], dn[4];
+};
+
+__device__ __forceinline__ unsigned fast_div(unsigned n, unsigned long long m, int sh) {
+  return (unsigned)(((unsigned long long)n * m) >> sh);
+}
+
+__device__ __forceinline__ Nbrs32 neighbours32(unsigned s, const LatticeGeom &g) {
+  Nbrs32 nb;
+  const unsigned L0 = g.L[0], L1 = g.L[1], L2 = g.L[2], L3 = g.L[3];
+  const unsigned q0 = fast_div(s, g.dm[0], g.dsh[0]);
+  const unsigned x = s - q0 * L0;
+  const unsigned q1 = fast_div(q0, g.dm[1], g.dsh[1]);
+  const unsigned y = q0 - q1 * L1;
+  const unsigned t = fast_div(q1, g.dm[2], g.dsh[2]);
+  const unsigned z = q1 - t * L2;
+  const unsigned sy = L0, sz = sy * L1, st = sz * L2;
+  nb.up[0] = x + 1 == L0 ? s - (L0 - 1) : s + 1;
+  nb.dn[0] = x == 0 ? s + (L0 - 1) : s - 1;
+  nb.up[1] = y + 1 == L1 ? s - (L1 - 1) * sy : s + sy;
+  nb.dn[1] = y == 0 ? s + (L1 - 1) * sy : s - sy;
+  nb.up[2] = z + 1 == L2 ? s - (L2 - 1) * sz : s + sz;
+  nb.dn[2] = z == 0 ? s + (L2 - 1) * sz : s - sz;
+  nb.up[3] = t + 1 == L3 ? s - (L3 - 1) * st : s + st;
+  nb.dn[3] = t == 0 ? s + (L3 - 1) * st : s - st;
   return nb;
 }
 
