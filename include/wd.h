@@ -241,11 +241,13 @@ int wd_set_f32_shape(wd_handle h, int nrhs, int R, int threads);
  * refreshed in FP64 and the BiCGStab recurrence continues with the replaced
  * residual.  0 < delta < 1: restarted refinement -- the low-precision
  * BiCGStab runs until its recursive residual has fallen by delta (or
- * max_inner iterations pass; 300 until set), then the FP64 residual is recomputed and the
+ * max_inner iterations pass), then the FP64 residual is recomputed and the
  * recurrence restarts from it (r_hat = r, p = v = 0).  Reliable updates keep
- * the Krylov space and are fastest on well-conditioned systems; restarted
- * refinement converges where the low-precision recurrence loses too much
- * accuracy (e.g. twisted mass near kappa_c).  Applies to
+ * the Krylov space across refreshes; restarted refinement converges where the
+ * low-precision recurrence loses too much accuracy (e.g. twisted mass near
+ * kappa_c), and restarting at least every few hundred iterations (the
+ * handle's initial max_inner is 300) also ends BiCGStab stagnation there.
+ * Applies to
  * dbicgstab_solve_mixed and tm_multishift_solve with mixed = 1; wd_stats
  * .restarts counts the restarts.  WD_BAD_ARG for delta outside [0, 1) or
  * max_inner < 1 with delta > 0. */
