@@ -23,7 +23,9 @@ def main(argv=None):
     from inputs import lattice as L
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", choices=["f64", "f32", "f16"], default="f32")
+    ap.add_argument("--kernel", choices=["f64", "f32", "f16", "mixed"], default="f32",
+                    help="a Wilson apply, or 'mixed': --reps iterations of the FP32 mixed "
+                         "BiCGStab on --nrhs sources (its vector updates and Wilson kernels)")
     ap.add_argument("--lattice", type=int, nargs=4, default=[20, 20, 20, 32])
     ap.add_argument("--nrhs", type=int, default=12)
     ap.add_argument("--reps", type=int, default=5)
@@ -35,6 +37,14 @@ def main(argv=None):
     op = wdl.WilsonOperator(dims, torch.from_numpy(U).cuda(), args.kappa)
     x = torch.from_numpy(psi).cuda()
     y = torch.empty_like(x)
+    if args.kernel == "mixed":
+        y.zero_()
+        rc, sts = op.dbicgstab_mixed(x, y, None, tol=1e-30, max_iter=args.reps)
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel": "mixed", "lattice": list(dims), "nrhs": args.nrhs,
+                          "iters": [q["iters"] for q in sts], "status": rc}))
+        op.close()
+        return
     fn = {"f64": op.apply, "f32": op.apply_f32, "f16": op.apply_f16}[args.kernel]
     fn(x, y)
     torch.cuda.synchronize()
