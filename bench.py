@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -124,7 +125,8 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        out_dir = os.environ.get("WD_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"clocks_rank{index}.csv")
 
     def start(self):
         try:
@@ -176,7 +178,7 @@ def _oracle_sample(cfg_name, kappa, budget_s):
     # BiCGStab iteration: 2 applies + the vector updates and dots of the oracle
     from oracle import krylov
     ti = []
-    while not ti or (time.perf_counter() - t0 < budget_s / 2 and len(ti) < 5):
+    while not ti or (time.perf_counter() - t0 < budget_s / 2 and len(ti) < 12):
         t = time.perf_counter()
         krylov.bicgstab(A, b, tol=1e-300, max_iter=2, max_restarts=0)
         ti.append((time.perf_counter() - t) / 2)

@@ -13,7 +13,7 @@
 Vectors are flat complex128 arrays of length n = 12 V; a basis is stored as
 rows (shape (k, n)).  ``apply`` is any callable x -> A x.
 
-Readings where the paper is silent (listed in the design doc as well):
+Readings where the paper is silent:
   * Inner products are <a, b> = a^dagger b (np.vdot).
   * Residuals are relative to ||b||; with x0 = 0 that is the paper's "norm
     of the initial residual" (Sec. 3).

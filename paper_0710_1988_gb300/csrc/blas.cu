@@ -386,24 +386,34 @@ ts_dot_kernel(const double2 *__restrict__ V, int k, const double2 *__restrict__ 
       }
     }
   }
-  // block reduction of the tile, fixed order
-  __shared__ double red[JT * RT * 2][TS_THREADS / 32];
+  // Block reduction of the tile, fixed order.  Within a warp the 32 doubles
+  // of the tile are reduced by recursive halving: at each of the five levels
+  // a lane keeps half of its values, sends the other half to its partner and
+  // adds what it receives, so lane i ends with the warp sum of value i after
+  // 16 + 8 + 4 + 2 + 1 additions (a shuffle tree per value would take 160).
+  static_assert(JT * RT * 2 == 32, "the tile holds 32 doubles");
+  __shared__ double red[32][TS_THREADS / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double vals[32];
 #pragma unroll
   for (int j = 0; j < JT; ++j)
 #pragma unroll
     for (int r = 0; r < RT; ++r) {
-      double a = acc[j][r].x, b = acc[j][r].y;
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, off);
-        b += __shfl_down_sync(0xffffffffu, b, off);
-      }
-      if (lane == 0) {
-        red[(j * RT + r) * 2][wid] = a;
-        red[(j * RT + r) * 2 + 1][wid] = b;
-      }
+      vals[(j * RT + r) * 2] = acc[j][r].x;
+      vals[(j * RT + r) * 2 + 1] = acc[j][r].y;
     }
+#pragma unroll
+  for (int lvl = 0; lvl < 5; ++lvl) {
+    const int half = 16 >> lvl;           // values kept after this level
+    const bool upper = (lane >> (4 - lvl)) & 1;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const double send = upper ? vals[i] : vals[i + half];
+      const double keep = upper ? vals[i + half] : vals[i];
+      vals[i] = keep + __shfl_xor_sync(0xffffffffu, send, half);
+    }
+  }
+  red[lane][wid] = vals[0];
   __syncthreads();
   const long long tile = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   for (int q = threadIdx.x; q < JT * RT; q += blockDim.x) {
