@@ -540,7 +540,7 @@ def main():
 
 # FP32 / FP16 bytes per site and system of the mixed solver's kernels
 LOW_DSLASH_BYTES = {32: 3 * 96, 16: 52 + 52 + 96}   # in + out + (r_hat or r) per site update
-LOW_LINK_BYTES = {32: 4 * 48, 16: 4 * 24}            # links, read once per launch
+LOW_LINK_BYTES = {32: 4 * 48, 16: 4 * 24}            # links (rows 0, 1), read once per launch
 LOW_UPDATE_BYTES = {32: 4 * 96 + 8 * 96,             # p = r + beta (p - omega v); x, r update
                     16: (96 + 3 * 52) + (4 * 96 + 3 * 52 + 2 * 96)}
 

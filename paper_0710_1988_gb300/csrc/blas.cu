@@ -426,22 +426,33 @@ ts_dot_kernel(const double2 *__restrict__ V, int k, const double2 *__restrict__ 
   }
 }
 
+// One warp per (j, r) pair: the lanes load the gx block partials of the pair
+// together (lane b, b + 32, ...) and reduce them with a fixed shuffle tree,
+// so the loads overlap instead of forming one dependent chain.
 __global__ void ts_dot_finalize_kernel(const double2 *__restrict__ partial, int gx, int gy,
                                        int JT, int RT, int k, int nrhs, double2 *C, int ldc,
                                        double2 *C2, int ldc2, const int *__restrict__ status) {
   if (status != nullptr && *status != 0) return;
   const int P = k * nrhs;
-  for (int pair = blockIdx.x * blockDim.x + threadIdx.x; pair < P;
-       pair += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int pair = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; pair < P; pair += warps) {
     const int j = pair / nrhs, r = pair % nrhs;
     const int ty = j / JT, jj = j % JT, tz = r / RT, rr = r % RT;
     const long long base = ((long long)tz * gy + ty) * gx;
     double2 t = make_double2(0.0, 0.0);
-    for (int b = 0; b < gx; ++b) t = cadd(t, partial[(base + b) * JT * RT + jj * RT + rr]);
-    C[(long long)j * ldc + r] = t;
-    if (C2 != nullptr) {
-      double2 &d = C2[(long long)j * ldc2 + r];
-      d = cadd(d, t);
+    for (int b = lane; b < gx; b += 32) t = cadd(t, partial[(base + b) * JT * RT + jj * RT + rr]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      t.x += __shfl_xor_sync(0xffffffffu, t.x, off);
+      t.y += __shfl_xor_sync(0xffffffffu, t.y, off);
+    }
+    if (lane == 0) {
+      C[(long long)j * ldc + r] = t;
+      if (C2 != nullptr) {
+        double2 &d = C2[(long long)j * ldc2 + r];
+        d = cadd(d, t);
+      }
     }
   }
 }
@@ -469,9 +480,9 @@ cudaError_t launch_ts_dot_finalize(const double2 *partial, long long n, int k, i
   ts_dot_grid(n, k, nrhs, &grid);
   int JT, RT;
   ts_dot_tile(nrhs, &JT, &RT);
-  const int P = k * nrhs;
-  ts_dot_finalize_kernel<<<(P + 127) / 128, 128, 0, s>>>(partial, grid.x, grid.y, JT, RT, k, nrhs,
-                                                         C, ldc, C2, ldc2, status);
+  const int P = k * nrhs;  // one warp per pair, four warps per block
+  ts_dot_finalize_kernel<<<(P + 3) / 4, 128, 0, s>>>(partial, grid.x, grid.y, JT, RT, k, nrhs,
+                                                     C, ldc, C2, ldc2, status);
   return cudaGetLastError();
 }
 
