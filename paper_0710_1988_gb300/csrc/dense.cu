@@ -477,26 +477,34 @@ __device__ int schur_block(double2 *A, double2 *Z, int m, int ld, double2 *u, lo
       } else if (wid != 3) {
         // Everything else of rotation kk, concurrently, on warps 0-2 and 4-6
         // (warp 3 idles so that the rotation warp's FP64 pipe is not shared,
-        // with warps assigned to the four schedulers round-robin): the row
-        // rotation on rows kk, kk+1 in the columns other than kk, kk+1
-        // (c0..kk-1 and kk+2..hi; the bulge entry (kk+1, kk-1) becomes 0), and
-        // the column rotation on rows l..kk-1.  The rotation warp's entries
-        // are disjoint from these.
+        // with warps assigned to the four schedulers round-robin):
+        //  - the row rotation on rows kk, kk+1 in the block's columns other
+        //    than kk, kk+1 (c0..kk-1 and kk+2..hi; the bulge entry
+        //    (kk+1, kk-1) becomes 0) and in the columns right of the block;
+        //  - the column rotation on rows l..kk-1, on the rows above the
+        //    block, and on the Schur vectors Z (all m rows).
+        // The rotation warp's entries are disjoint from these, and each
+        // entry outside the block sees the sweep's rotations in order.
         const int wk = (wid < 3 ? wid : wid - 1) * 32 + lane;
         const int c0 = kk > l ? kk - 1 : l;
-        const int ncols = hi - c0 - 1, nrows = kk - l;
-        for (int t = wk; t < ncols + nrows; t += nwk) {
-          if (t < ncols) {
-            const int j = c0 + t < kk ? c0 + t : c0 + t + 2;
+        const int ncols = hi - c0 - 1;          // block columns, row rotation
+        const int nright = m - 1 - hi;          // columns right of the block
+        const int nrows = kk;                   // rows 0..kk-1 (above and in the block)
+        const int nrot = ncols + nright;
+        for (int t = wk; t < nrot + nrows + m; t += nwk) {
+          if (t < nrot) {
+            const int j = t < ncols ? (c0 + t < kk ? c0 + t : c0 + t + 2) : hi + 1 + (t - ncols);
             const double2 a1 = A[kk * ld + j], a2 = A[(kk + 1) * ld + j];
             A[kk * ld + j] = cadd(cscale(gc, a1), cmul(gs, a2));
             A[(kk + 1) * ld + j] = (kk > l && j == kk - 1) ? make_double2(0.0, 0.0)
                                                            : cadd(cmul(mgs, a1), cscale(gc, a2));
           } else {
-            const int row = l + (t - ncols);
-            const double2 a1 = A[row * ld + kk], a2 = A[row * ld + kk + 1];
-            A[row * ld + kk] = cadd(cscale(gc, a1), cmul(cgs, a2));
-            A[row * ld + kk + 1] = cadd(cmul(ngs, a1), cscale(gc, a2));
+            const int q = t - nrot;
+            double2 *X = q < nrows ? A : Z;
+            const int row = q < nrows ? q : q - nrows;
+            const double2 a1 = X[row * ld + kk], a2 = X[row * ld + kk + 1];
+            X[row * ld + kk] = cadd(cscale(gc, a1), cmul(cgs, a2));
+            X[row * ld + kk + 1] = cadd(cmul(ngs, a1), cscale(gc, a2));
           }
         }
       }
@@ -506,30 +514,6 @@ __device__ int schur_block(double2 *A, double2 *Z, int m, int ld, double2 *u, lo
       const long long t1 = clock64();
       t_rot += t1 - t0;
       t0 = t1;
-    }
-    // deferred: rows above the block (column rotations), columns right of it
-    // (row rotations), and the Schur vectors (column rotations)
-    for (int t = tid; t < l + (m - 1 - hi) + m; t += bd) {
-      if (t < l || t >= l + (m - 1 - hi)) {
-        double2 *X = t < l ? A : Z;
-        const int row = t < l ? t : t - l - (m - 1 - hi);
-        for (int kk = l; kk < hi; ++kk) {
-          const double gc = s_gc[kk];
-          const double2 gs = s_gs[kk];
-          const double2 a1 = X[row * ld + kk], a2 = X[row * ld + kk + 1];
-          X[row * ld + kk] = cadd(cscale(gc, a1), cmul(cconj(gs), a2));
-          X[row * ld + kk + 1] = cadd(cmul(cneg(gs), a1), cscale(gc, a2));
-        }
-      } else {
-        const int col = hi + 1 + (t - l);
-        for (int kk = l; kk < hi; ++kk) {
-          const double gc = s_gc[kk];
-          const double2 gs = s_gs[kk];
-          const double2 a1 = A[kk * ld + col], a2 = A[(kk + 1) * ld + col];
-          A[kk * ld + col] = cadd(cscale(gc, a1), cmul(gs, a2));
-          A[(kk + 1) * ld + col] = cadd(cmul(cneg(cconj(gs)), a1), cscale(gc, a2));
-        }
-      }
     }
     __syncthreads();
     if (tid == 0) t_def += clock64() - t0;
