@@ -333,25 +333,40 @@ __device__ int schur_block(double2 *A, double2 *Z, int m, int ld, double2 *u, lo
   for (int e = tid; e < m * m; e += bd)
     Z[(e / m) * ld + e % m] = (e / m == e % m) ? make_double2(1.0, 0.0) : make_double2(0.0, 0.0);
   __syncthreads();
-  // Householder reduction to upper Hessenberg form
+  // Householder reduction to upper Hessenberg form.  Each reflector spans
+  // rows j+1 .. iend, iend the last nonzero row of column j: after a
+  // GMRES-DR restart only the leading (k+1) x k block is full, so the
+  // reflectors stop at row k instead of m - 1.  iend comes from a shared
+  // atomic maximum, triple-buffered so that no slot is reset while another
+  // thread may still read or update it.
+  __shared__ int s_end[3];
+  if (tid < 3) s_end[tid] = 0;
+  __syncthreads();
   for (int j = 0; j + 2 < m; ++j) {
+    const int slot = j % 3;
     double part = 0.0;
-    for (int i = j + 2 + tid; i < m; i += bd) part += cnorm2(A[i * ld + j]);
-    const double below = block_dsum_all(part);
+    for (int i = j + 2 + tid; i < m; i += bd) {
+      const double2 d = A[i * ld + j];
+      part += cnorm2(d);
+      if (d.x != 0.0 || d.y != 0.0) atomicMax(&s_end[slot], i);
+    }
+    const double below = block_dsum_all(part);  // its barriers order the atomics
+    const int iend = s_end[slot];
+    if (tid == 0) s_end[(j + 2) % 3] = 0;
     if (below == 0.0) continue;
     const double2 al = A[(j + 1) * ld + j];
     const double aa = cabs_(al), nx = sqrt(below + aa * aa);
     const double2 ph = aa > 0.0 ? cscale(1.0 / aa, al) : make_double2(1.0, 0.0);
     const double2 beta = cscale(-nx, ph);
-    for (int i = j + 1 + tid; i < m; i += bd) u[i] = i == j + 1 ? csub(al, beta) : A[i * ld + j];
+    for (int i = j + 1 + tid; i <= iend; i += bd) u[i] = i == j + 1 ? csub(al, beta) : A[i * ld + j];
     __syncthreads();
     const double tau = 1.0 / (nx * (nx + aa));
-    reflect_left(A, ld, u, tau, j + 1, m - 1, j, m);
+    reflect_left(A, ld, u, tau, j + 1, iend, j, m);
     __syncthreads();
-    reflect_right(A, ld, u, tau, j + 1, m - 1, 0, m);
-    reflect_right(Z, ld, u, tau, j + 1, m - 1, 0, m);
+    reflect_right(A, ld, u, tau, j + 1, iend, 0, m);
+    reflect_right(Z, ld, u, tau, j + 1, iend, 0, m);
     __syncthreads();
-    for (int i = j + 1 + tid; i < m; i += bd)
+    for (int i = j + 1 + tid; i <= iend; i += bd)
       A[i * ld + j] = i == j + 1 ? beta : make_double2(0.0, 0.0);
     __syncthreads();
   }
@@ -384,7 +399,7 @@ __device__ int schur_block(double2 *A, double2 *Z, int m, int ld, double2 *u, lo
   __shared__ double2 s_gs[CE_MAXM];
   __shared__ int s_l[2];    // deflation point of the scan, double-buffered
   const int rt = bd - 32;   // first thread of the rotation warp (the last warp)
-  const int nwk = bd - 64;  // threads of the bulk updates (all warps but 3 and the last)
+  const int nwk = bd - 32;  // threads of the bulk updates (all warps but the last)
   const int wid = tid >> 5, lane = tid & 31;
   long long rotations = 0, t_scan = 0, t_rot = 0, t_def = 0, t0 = 0;
   int hi = m - 1, its = 0, total = 0, scan = 0;
@@ -474,10 +489,11 @@ __device__ int schur_block(double2 *A, double2 *Z, int m, int ld, double2 *u, lo
         y.x = __shfl_sync(0xffffffffu, o.x, 4);
         y.y = __shfl_sync(0xffffffffu, o.y, 4);
         if (ln == 0 && kk + 1 < hi) givens(x, y, s_gc[kk + 1], s_gs[kk + 1]);
-      } else if (wid != 3) {
-        // Everything else of rotation kk, concurrently, on warps 0-2 and 4-6
-        // (warp 3 idles so that the rotation warp's FP64 pipe is not shared,
-        // with warps assigned to the four schedulers round-robin):
+      } else {
+        // Everything else of rotation kk, concurrently, on the other seven
+        // warps; warps 0-2 and 4-6 take the first 192 entries and warp 3
+        // (which shares a scheduler with the rotation warp when warps are
+        // assigned to the four schedulers round-robin) only the overflow:
         //  - the row rotation on rows kk, kk+1 in the block's columns other
         //    than kk, kk+1 (c0..kk-1 and kk+2..hi; the bulge entry
         //    (kk+1, kk-1) becomes 0) and in the columns right of the block;
@@ -485,7 +501,7 @@ __device__ int schur_block(double2 *A, double2 *Z, int m, int ld, double2 *u, lo
         //    block, and on the Schur vectors Z (all m rows).
         // The rotation warp's entries are disjoint from these, and each
         // entry outside the block sees the sweep's rotations in order.
-        const int wk = (wid < 3 ? wid : wid - 1) * 32 + lane;
+        const int wk = wid == 3 ? 192 + lane : (wid < 3 ? wid : wid - 1) * 32 + lane;
         const int c0 = kk > l ? kk - 1 : l;
         const int ncols = hi - c0 - 1;          // block columns, row rotation
         const int nright = m - 1 - hi;          // columns right of the block
