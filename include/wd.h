@@ -195,6 +195,13 @@ int dbicgstab_solve_adjoint(wd_handle h, wd_deflation d, const void *G, void *LA
                             int nrhs, double tol, int max_iter, wd_stats *stats,
                             wd_stream stream);
 
+/* The same adjoint solve through the mixed-precision solver
+ * (dbicgstab_solve_mixed: FP32 or FP16 iteration per wd_set_mixed_storage,
+ * strategy per wd_set_mixed_restart, FP64 true residual <= tol). */
+int dbicgstab_solve_adjoint_mixed(wd_handle h, wd_deflation d, const void *G, void *LAM,
+                                  int nrhs, double tol, int max_iter, int reliable_every,
+                                  wd_stats *stats, wd_stream stream);
+
 /* For L real with dL = Re(g^dagger dx), x = A^{-1} b and lam = A^{-dagger} g:
  *  force  (NULL or device, V*4*8 double, [site][mu][a]): dL/domega for links
  *         moved as U_mu(s) -> exp(i omega_a lambda_a/2) U_mu(s) (Gell-Mann

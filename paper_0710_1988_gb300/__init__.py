@@ -178,13 +178,21 @@ class WilsonOperator:
         return rc, [s.as_dict() for s in sts]
 
     def adjoint_solve(self, G, LAM, deflation: Optional["Deflation"] = None,
-                      tol: float = 1e-10, max_iter: int = 100000, stream=None):
-        """LAM = A^{-dagger} G (gamma5 A(-mu)^{-1} gamma5 G) for every column of G."""
+                      tol: float = 1e-10, max_iter: int = 100000, mixed: bool = False,
+                      reliable_every: int = 50, stream=None):
+        """LAM = A^{-dagger} G (gamma5 A(-mu)^{-1} gamma5 G) for every column of G;
+        mixed = True solves with the mixed-precision solver."""
         nrhs = self._nrhs(G)
         sts = (WdStats * nrhs)()
-        rc = lib().dbicgstab_solve_adjoint(
-            self._h, deflation._d if deflation is not None else None, _ptr(G), _ptr(LAM), nrhs,
-            float(tol), int(max_iter), sts, _stream(stream, G, LAM))
+        d = deflation._d if deflation is not None else None
+        if mixed:
+            rc = lib().dbicgstab_solve_adjoint_mixed(
+                self._h, d, _ptr(G), _ptr(LAM), nrhs, float(tol), int(max_iter),
+                int(reliable_every), sts, _stream(stream, G, LAM))
+        else:
+            rc = lib().dbicgstab_solve_adjoint(
+                self._h, d, _ptr(G), _ptr(LAM), nrhs, float(tol), int(max_iter), sts,
+                _stream(stream, G, LAM))
         check(rc, allow=(_lib.WD_OK, _lib.WD_NOT_CONVERGED, _lib.WD_BREAKDOWN))
         return rc, [s.as_dict() for s in sts]
 

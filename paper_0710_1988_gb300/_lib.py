@@ -74,6 +74,7 @@ SIGNATURES = {
     "dbicgstab_solve_deflated": (I, [P, P, P, P, I, D, I, ctypes.POINTER(WdStats), P]),
     "dbicgstab_solve": (I, [P, P, P, I, P, P, I, D, I, ctypes.POINTER(WdStats), P]),
     "dbicgstab_solve_adjoint": (I, [P, P, P, P, I, D, I, ctypes.POINTER(WdStats), P]),
+    "dbicgstab_solve_adjoint_mixed": (I, [P, P, P, P, I, D, I, I, ctypes.POINTER(WdStats), P]),
     "wd_gradients": (I, [P, P, P, P, ctypes.POINTER(D), P]),
     "tm_multishift_solve": (I, [P, P, P, I, ctypes.POINTER(D), I, D, I, I, I, ctypes.POINTER(WdStats), P]),
     "dbicgstab_solve_mixed": (I, [P, P, P, P, I, D, I, I, ctypes.POINTER(WdStats), P]),

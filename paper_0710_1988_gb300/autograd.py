@@ -15,26 +15,31 @@ import torch
 
 
 class WilsonSolve(torch.autograd.Function):
-    """x = WilsonSolve.apply(b, kappa, omega, op, deflation, tol, max_iter).
+    """x = WilsonSolve.apply(b, kappa, omega, op, deflation, tol, max_iter, mixed).
 
     b: complex128 CUDA tensor (12V elements).  kappa: 0-dim float64 tensor,
     equal to op.kappa.  omega: float64 tensor of shape (V, 4, 8), all zero: the
     Lie-algebra coordinates of the links around the operator's own links
     (U -> exp(i omega_a lambda_a / 2) U); its gradient is the link force.
+    mixed: solve forward and adjoint with the mixed-precision solver (FP32 or
+    FP16 iteration, FP64 true residual); the gradients are formed in FP64.
     """
 
     @staticmethod
-    def forward(ctx, b, kappa, omega, op, deflation=None, tol=1e-10, max_iter=100000):
+    def forward(ctx, b, kappa, omega, op, deflation=None, tol=1e-10, max_iter=100000,
+                mixed=False):
         if abs(float(kappa) - op.kappa) > 1e-15 * max(1.0, abs(op.kappa)):
             raise ValueError("kappa must equal the operator's kappa")
         if omega.abs().max().item() != 0.0:
             raise ValueError("omega must be zero: the gradient is taken at the operator's links")
         x = torch.zeros_like(b)
-        rc, st = op.dbicgstab(b.contiguous(), x, deflation, tol=tol, max_iter=max_iter)
+        solve = op.dbicgstab_mixed if mixed else op.dbicgstab
+        rc, st = solve(b.contiguous(), x, deflation, tol=tol, max_iter=max_iter)
         if rc != 0:
             raise RuntimeError(f"forward solve failed (status {rc})")
         ctx.save_for_backward(x)
         ctx.op, ctx.deflation, ctx.tol, ctx.max_iter = op, deflation, tol, max_iter
+        ctx.mixed = mixed
         ctx.omega_shape = omega.shape
         return x
 
@@ -44,7 +49,7 @@ class WilsonSolve(torch.autograd.Function):
         op = ctx.op
         lam = torch.zeros_like(g)
         rc, st = op.adjoint_solve(g.contiguous(), lam, ctx.deflation, tol=ctx.tol,
-                                  max_iter=ctx.max_iter)
+                                  max_iter=ctx.max_iter, mixed=ctx.mixed)
         if rc != 0:
             raise RuntimeError(f"adjoint solve failed (status {rc})")
         want_k = ctx.needs_input_grad[1]
@@ -54,8 +59,8 @@ class WilsonSolve(torch.autograd.Function):
         dk = op.gradients(lam, x, force=force, want_dkappa=want_k) if (want_k or want_w) else None
         grad_b = lam if ctx.needs_input_grad[0] else None
         grad_k = torch.tensor(dk, dtype=torch.float64) if want_k else None
-        return grad_b, grad_k, force, None, None, None, None
+        return grad_b, grad_k, force, None, None, None, None, None
 
 
-def wilson_solve(b, kappa, omega, op, deflation=None, tol=1e-10, max_iter=100000):
-    return WilsonSolve.apply(b, kappa, omega, op, deflation, tol, max_iter)
+def wilson_solve(b, kappa, omega, op, deflation=None, tol=1e-10, max_iter=100000, mixed=False):
+    return WilsonSolve.apply(b, kappa, omega, op, deflation, tol, max_iter, mixed)

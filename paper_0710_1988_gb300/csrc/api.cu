@@ -520,9 +520,11 @@ extern "C" int tm_multishift_solve(wd_handle h, const void *B, void *X, int nrhs
 
 // ------------------------------------------------------------------ differentiation
 
-extern "C" int dbicgstab_solve_adjoint(wd_handle h, wd_deflation d, const void *G, void *LAM,
-                                       int nrhs, double tol, int max_iter, wd_stats *stats,
-                                       wd_stream stream) {
+// LAM = gamma5 A(-mu)^{-1} gamma5 G with the FP64 (mixed = false) or the
+// mixed-precision solver.
+static int adjoint_solve(wd_handle h, wd_deflation d, const void *G, void *LAM, int nrhs,
+                         double tol, int max_iter, int mixed, int reliable_every,
+                         wd_stats *stats, wd_stream stream) {
   if (h == nullptr || G == nullptr || LAM == nullptr) return bad("dbicgstab_solve_adjoint: NULL argument");
   if (nrhs < 1 || nrhs > 65535) return bad("dbicgstab_solve_adjoint: nrhs must be in [1, 65535]");
   if (!is_device_pointer(G) || !is_device_pointer(LAM)) return bad("dbicgstab_solve_adjoint: G and LAM must be device memory");
@@ -542,7 +544,8 @@ extern "C" int dbicgstab_solve_adjoint(wd_handle h, wd_deflation d, const void *
   }
   const double mu = h->mu;
   h->mu = -mu;
-  int rc = dbicgstab_solve_deflated(h, d, t, LAM, nrhs, tol, max_iter, stats, stream);
+  int rc = mixed ? dbicgstab_solve_mixed(h, d, t, LAM, nrhs, tol, max_iter, reliable_every, stats, stream)
+                 : dbicgstab_solve_deflated(h, d, t, LAM, nrhs, tol, max_iter, stats, stream);
   h->mu = mu;
   if (rc == WD_OK || rc == WD_NOT_CONVERGED || rc == WD_BREAKDOWN) {
     e = cudaMemcpyAsync(t, LAM, sizeof(double2) * nn, cudaMemcpyDeviceToDevice, s);
@@ -553,6 +556,18 @@ extern "C" int dbicgstab_solve_adjoint(wd_handle h, wd_deflation d, const void *
   ar.release();
   cudaStreamSynchronize(s);
   return rc;
+}
+
+extern "C" int dbicgstab_solve_adjoint(wd_handle h, wd_deflation d, const void *G, void *LAM,
+                                       int nrhs, double tol, int max_iter, wd_stats *stats,
+                                       wd_stream stream) {
+  return adjoint_solve(h, d, G, LAM, nrhs, tol, max_iter, 0, 0, stats, stream);
+}
+
+extern "C" int dbicgstab_solve_adjoint_mixed(wd_handle h, wd_deflation d, const void *G, void *LAM,
+                                             int nrhs, double tol, int max_iter, int reliable_every,
+                                             wd_stats *stats, wd_stream stream) {
+  return adjoint_solve(h, d, G, LAM, nrhs, tol, max_iter, 1, reliable_every, stats, stream);
 }
 
 extern "C" int wd_gradients(wd_handle h, const void *lam, const void *x, void *force,

@@ -139,3 +139,35 @@ def test_adjoint_solve_uses_the_deflation_space(wdl):
     assert np.linalg.norm(r) <= 1.05e-10 * np.linalg.norm(host(g))
     defl.close()
     op.close()
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.05])
+def test_mixed_autograd_matches_oracle(wdl, mu):
+    """The autograd Function with mixed = True (FP32 iteration, restarted
+    refinement, FP64 true residual 1e-12 for both solves): dL/db, dL/dkappa
+    and the link force against the oracle's gradient (bars as the FP64 path
+    at its 1e-13 solves, relaxed 10x for the 1e-12 ones)."""
+    import torch
+    from paper_0710_1988_gb300.autograd import wilson_solve
+    dims = (4, 4, 4, 8)
+    U = L.gauge_field(dims, 0.5, 5000)
+    kappa = 0.13
+    b_h = L.gaussian_spinor(dims, 5001).ravel()
+    eta_h = L.gaussian_spinor(dims, 5002).ravel()
+    Lo, lam_o, dk_o, f_o = _oracle_grads(U, dims, kappa, b_h, eta_h, mu)
+    op = wdl.WilsonOperator(dims, cuda(U), kappa, mu)
+    op.set_mixed_restart(1e-3)
+    b = cuda(b_h).requires_grad_(True)
+    kap = torch.tensor(kappa, dtype=torch.float64, requires_grad=True)
+    om = torch.zeros((L.volume(dims), 4, 8), dtype=torch.float64, device="cuda:0",
+                     requires_grad=True)
+    x = wilson_solve(b, kap, om, op, None, 1e-12, 100000, mixed=True)
+    loss = torch.real(torch.vdot(cuda(eta_h), x))
+    loss.backward()
+    assert abs(loss.item() - Lo) <= 1e-9 * abs(Lo)
+    lam_h = host(b.grad)
+    assert np.linalg.norm(lam_h - lam_o) <= 1e-8 * np.linalg.norm(lam_o)
+    assert abs(kap.grad.item() - dk_o) <= 1e-7 * abs(dk_o)
+    fh = host(om.grad)
+    assert np.linalg.norm(fh - f_o) <= 1e-7 * np.linalg.norm(f_o)
+    op.close()
