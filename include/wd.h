@@ -220,14 +220,17 @@ int wd_gradients(wd_handle h, const void *lam, const void *x, void *force,
  * recomputed with the FP64 operator.  The deflation projection (Sec. 2)
  * and the convergence test (FP64 true residual <= tol) are FP64.  Arguments
  * and results as dbicgstab_solve_deflated; reliable_every >= 1 (50 is the
- * workload's choice).  Not in the paper, which states no precision. */
+ * workload's choice).  Not in the paper, which states no precision.  In
+ * even-odd mode the iteration runs on the Schur operator (FP32 storage
+ * only; B and X are the prepared even half vectors, as for the FP64 solver). */
 int dbicgstab_solve_mixed(wd_handle h, wd_deflation d, const void *B, void *X,
                           int nrhs, double tol, int max_iter, int reliable_every,
                           wd_stats *stats, wd_stream stream);
 
 /* out = A in (dagger = 0) or A^dagger in, computed by the FP32 kernel of
  * the mixed solver: in and out are FP64 device vectors in the boundary
- * layout, rounded to FP32 on entry and widened on exit. */
+ * layout, rounded to FP32 on entry and widened on exit.  In even-odd mode
+ * (wd_set_operator(h, 1)) A is the Schur operator on even half vectors. */
 int wd_apply_f32(wd_handle h, const void *in, void *out, int nrhs, int dagger,
                  wd_stream stream);
 

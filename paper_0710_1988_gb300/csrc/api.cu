@@ -614,7 +614,8 @@ extern "C" int dbicgstab_solve_mixed(wd_handle h, wd_deflation d, const void *B,
                                      wd_stats *stats, wd_stream stream) {
   ProfScope prof_scope_(h ? &h->prof : nullptr);
   if (h == nullptr) return bad("dbicgstab_solve_mixed: NULL handle");
-  if (h->eo) return bad("dbicgstab_solve_mixed: the FP32 path acts on the full operator");
+  if (h->eo && h->mixed_bits != 32)
+    return bad("dbicgstab_solve_mixed: with even-odd only FP32 storage is available");
   if (B == nullptr || X == nullptr) return bad("dbicgstab_solve_mixed: NULL B or X");
   if (nrhs < 1 || nrhs > 65535) return bad("dbicgstab_solve_mixed: nrhs must be in [1, 65535]");
   if (!(tol > 0.0)) return bad("dbicgstab_solve_mixed: tol must be positive");
@@ -637,7 +638,7 @@ extern "C" int dbicgstab_solve_mixed(wd_handle h, wd_deflation d, const void *B,
     cudaEventRecord(h->ev_in, caller);
     cudaStreamWaitEvent(s, h->ev_in, 0);
   }
-  const long long n = h->n;
+  const long long n = op_n(h);
   Arena ar;
   ar.pool = h->pool;
   ar.stream = s;
@@ -706,7 +707,6 @@ extern "C" int wd_apply_f32(wd_handle h, const void *in, void *out, int nrhs, in
                             wd_stream stream) {
   ProfScope prof_scope_(h ? &h->prof : nullptr);
   if (h == nullptr) return bad("wd_apply_f32: NULL handle");
-  if (h->eo) return bad("wd_apply_f32: the FP32 kernel acts on the full operator");
   if (in == nullptr || out == nullptr) return bad("wd_apply_f32: NULL vector");
   if (nrhs < 1 || nrhs > 65535) return bad("wd_apply_f32: nrhs must be in [1, 65535]");
   if (!is_device_pointer(in) || !is_device_pointer(out))
@@ -717,16 +717,20 @@ extern "C" int wd_apply_f32(wd_handle h, const void *in, void *out, int nrhs, in
   Arena ar;
   ar.pool = h->pool;
   ar.stream = s;
-  const size_t v32 = (size_t)nrhs * 6 * h->V;
+  const long long Vop = h->eo ? h->V / 2 : h->V;  // even half vectors in even-odd mode
+  const size_t v32 = (size_t)nrhs * 6 * Vop;
   float4 *a = ar.take<float4>(v32), *b = ar.take<float4>(v32);
+  float4 *tmp = h->eo ? ar.take<float4>(v32) : nullptr;
   if (ar.failed) return bad_alloc();
   const Mixed32 m{h, h->links32};
-  cudaError_t e = launch_f64_to_f32(static_cast<const double2 *>(in), a, h->V, nrhs, nullptr,
+  cudaError_t e = launch_f64_to_f32(static_cast<const double2 *>(in), a, Vop, nrhs, nullptr,
                                     nullptr, nullptr, M_ALL, s);
   if (e == cudaSuccess)
-    e = launch_wilson_f32(m, a, nullptr, b, nrhs, dagger ? 1 : 0, EPI_NONE, nullptr, nullptr,
-                          nullptr, nullptr, M_ALL, s);
-  if (e == cudaSuccess) e = launch_f32_to_f64(b, static_cast<double2 *>(out), h->V, nrhs, s);
+    e = h->eo ? launch_schur_f32(m, a, nullptr, b, tmp, nrhs, dagger ? 1 : 0, EPI_NONE, nullptr,
+                                 nullptr, nullptr, nullptr, M_ALL, s)
+              : launch_wilson_f32(m, a, nullptr, b, nrhs, dagger ? 1 : 0, EPI_NONE, nullptr,
+                                  nullptr, nullptr, nullptr, M_ALL, s);
+  if (e == cudaSuccess) e = launch_f32_to_f64(b, static_cast<double2 *>(out), Vop, nrhs, s);
   ar.release();
   if (e != cudaSuccess) return cuda_fail(e, "wd_apply_f32");
   return WD_OK;

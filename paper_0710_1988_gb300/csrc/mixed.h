@@ -78,6 +78,15 @@ cudaError_t launch_bicg16_restart(float4 *rhat, const float4 *r, Half16 p, Half1
                                   const int *status, unsigned mask, long long V, int nrhs,
                                   cudaStream_t s);
 
+// ----------------------------------------------------------------- FP32 Schur operator (mixed_eo.cu)
+// out = A_hat in on even half vectors (float4 [rhs][6][V/2]); tmp: an odd
+// half vector per system; epi / FUSED as launch_wilson_f32.
+int schur32_blocks(const wd_context *h);
+cudaError_t launch_schur_f32(const Mixed32 &m, const float4 *in, const float4 *in2, float4 *out,
+                             float4 *tmp, int nrhs, int dagger, int epi, const BicgScalars *sc,
+                             const float4 *aux, double *partial, const int *status,
+                             unsigned mask, cudaStream_t s);
+
 cudaError_t launch_reliable_finalize(const double *partial, int nb, BicgScalars *sc, int *status,
                                      unsigned mask, int nrhs, cudaStream_t s, int force = 0);
 cudaError_t launch_mixed_inner_tol(BicgScalars *sc, const int *status, int nrhs, cudaStream_t s);

@@ -52,10 +52,6 @@ int ensure_links32(wd_context *h, cudaStream_t s) {
     set_error("the FP32/FP16 kernels index sites with 32 bits: fewer than 2^31 sites");
     return WD_BAD_ARG;
   }
-  if (h->eo) {
-    set_error("the FP32 kernels act on the full operator: switch the handle back with wd_set_operator(h, 0)");
-    return WD_BAD_ARG;
-  }
   if (h->links32 != nullptr) return WD_OK;
   WD_CK(cudaMalloc(&h->links32, sizeof(float4) * 12 * h->V));
   WD_CK(launch_links_to_f32(h, h->links32, s));
@@ -81,8 +77,13 @@ int bicgstab_mixed_batched(wd_context *h, const double2 *B, double2 *X, const do
                            int nrhs, double tol, int max_iter, int reliable_every,
                            wd_stats *stats, cudaStream_t s, Arena &ar) {
   const bool half = h->mixed_bits == 16;
+  const bool eo = h->eo != 0;  // FP32 only: the Schur operator on even half vectors
+  if (eo && half) {
+    set_error("FP16 storage acts on the full operator: use FP32 storage with even-odd");
+    return WD_BAD_ARG;
+  }
   RET_IF(half ? ensure_links16(h, s) : ensure_links32(h, s));
-  const long long V = h->V, n = h->n, n4 = 6 * V;
+  const long long V = eo ? h->V / 2 : h->V, n = op_n(h), n4 = 6 * V;
   const size_t v32 = (size_t)nrhs * n4, nv = (size_t)nrhs * V;
   float4 *r = ar.take<float4>(v32), *rhat = ar.take<float4>(v32), *xs = ar.take<float4>(v32);
   float4 *p = nullptr, *v = nullptr, *t = nullptr;
@@ -97,9 +98,10 @@ int bicgstab_mixed_batched(wd_context *h, const double2 *B, double2 *X, const do
     t = ar.take<float4>(v32);
   }
   double2 *r64 = ar.take<double2>((size_t)nrhs * n), *tmp64 = ar.take<double2>((size_t)nrhs * n);
+  float4 *tmp_o = eo ? ar.take<float4>(v32) : nullptr;  // odd half vectors of the Schur operator
   {  // pick the Wilson kernel's launch shape for this nrhs once per handle
     const int key = nrhs < WD_TUNE_SLOTS ? nrhs : WD_TUNE_SLOTS - 1;
-    if (!half && h->tune_R[key] == 0 && !ar.failed) {
+    if (!half && !eo && h->tune_R[key] == 0 && !ar.failed) {
       WD_CK(cudaMemsetAsync(r, 0, sizeof(float4) * v32, s));
       WD_CK(tune_wilson_f32(h, h->links32, nrhs, r, v, s));
     }
@@ -109,7 +111,7 @@ int bicgstab_mixed_batched(wd_context *h, const double2 *B, double2 *X, const do
       WD_CK(tune_wilson_f16(h, h->links16, nrhs, p16, v16, s));
     }
   }
-  const int nbw = half ? wilson16_blocks(h, nrhs) : wilson32_blocks(h, nrhs);
+  const int nbw = eo ? schur32_blocks(h) : half ? wilson16_blocks(h, nrhs) : wilson32_blocks(h, nrhs);
   const int nbs = half ? stream16_blocks(V) : stream32_blocks(n4), nbc = conv_blocks_count(V);
   const int nb64 = stream_blocks(n);
   double *part_w = ar.take<double>((size_t)nrhs * nbw * 3);
@@ -161,11 +163,16 @@ int bicgstab_mixed_batched(wd_context *h, const double2 *B, double2 *X, const do
         RET_IF(ok(launch_wilson_f16(h, h->links16, p16, nullptr, v16, nrhs, 0, EPI_DOT, sc, rhat, part_w, status, M_ACTIVE, s), "w16_dot"));
       } else {
         RET_IF(ok(launch_bicg32_update_p(p, r, v, sc, status, n4, nrhs, s), "update_p32"));
-        RET_IF(ok(launch_wilson_f32(m, p, nullptr, v, nrhs, 0, EPI_DOT, sc, rhat, part_w, status, M_ACTIVE, s), "w32_dot"));
+        if (eo)
+          RET_IF(ok(launch_schur_f32(m, p, nullptr, v, tmp_o, nrhs, 0, EPI_DOT, sc, rhat, part_w, status, M_ACTIVE, s), "s32_dot"));
+        else
+          RET_IF(ok(launch_wilson_f32(m, p, nullptr, v, nrhs, 0, EPI_DOT, sc, rhat, part_w, status, M_ACTIVE, s), "w32_dot"));
       }
       RET_IF(ok(launch_bicg_finalize(FIN_ALPHA, part_w, nbw, sc, status, nullptr, 0, nrhs, s), "fin_alpha"));
       if (half)
         RET_IF(ok(launch_wilson_f16(h, h->links16, v16, r, t16, nrhs, 0, EPI_TSTT, sc, nullptr, part_w, status, M_ACTIVE, s), "w16_tstt"));
+      else if (eo)
+        RET_IF(ok(launch_schur_f32(m, r, v, t, tmp_o, nrhs, 0, EPI_TSTT, sc, nullptr, part_w, status, M_ACTIVE, s), "s32_tstt"));
       else
         RET_IF(ok(launch_wilson_f32(m, r, v, t, nrhs, 0, EPI_TSTT, sc, nullptr, part_w, status, M_ACTIVE, s), "w32_tstt"));
       RET_IF(ok(launch_bicg_finalize(FIN_OMEGA, part_w, nbw, sc, status, nullptr, 0, nrhs, s), "fin_omega"));
