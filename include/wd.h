@@ -94,8 +94,10 @@ int wd_create(const int lat[4], const void *links, double kappa, double mu,
  *   A_hat = (1 + i mu gamma5) - kappa^2 D_eo (1 + i mu gamma5)^{-1} D_oe,
  * on even-site half vectors (n = 6 V complex128, site s of parity 0 stored at
  * s / 2).  Needs all extents even.  wd_apply, gmresdr_solve, the deflation
- * and D-BiCGStab entry points and tm_multishift_solve then use A_hat and
- * half vectors; the FP32 path and wd_gradients need even_odd = 0. */
+ * and D-BiCGStab entry points then use A_hat and half vectors (the mixed
+ * solver with FP32 storage as well); tm_multishift_solve keeps full-lattice
+ * vectors and solves each shift through A_hat (see there); the FP16
+ * kernels, wd_gradients and wd_apply_f32_noalloc need even_odd = 0. */
 int wd_set_operator(wd_handle h, int even_odd);
 
 /* Even-odd helpers (handle in even-odd mode; device pointers; nrhs vectors):
@@ -178,7 +180,12 @@ int dbicgstab_solve(wd_handle h, const void *B, void *X, int nrhs,
  * The handle's kappa is used for every shift; its mu is restored on return.
  *  B: device, nrhs*n complex128.  X: device, nshift*nrhs*n complex128,
  *  X[i][r] = solution of shift i, right-hand side r.  mus: host, nshift.
- *  stats: NULL or host array of nshift*nrhs, [i][r]. */
+ *  stats: NULL or host array of nshift*nrhs, [i][r].
+ * In even-odd mode B and X stay full-lattice vectors (n = 12 V): each
+ * shift's source is prepared with that shift's mu, the Schur system is
+ * solved (projected over the earlier shifts' even-site solutions; mixed = 1
+ * needs FP32 storage) and the solution is reconstructed; tol applies to the
+ * Schur residual. */
 int tm_multishift_solve(wd_handle h, const void *B, void *X, int nrhs,
                         const double *mus, int nshift, double tol, int max_iter,
                         int project, int mixed, wd_stats *stats, wd_stream stream);

@@ -212,8 +212,13 @@ class WilsonOperator:
                    project: bool = True, mixed: bool = False, stream=None):
         """Sec. 4: A(mu_i) X[i] = B for the shifts in the given order, each
         projected over the earlier solutions.  X holds len(mus)*nrhs*12V
-        complex128 ([shift][rhs][...]).  Returns (status, stats [shift][rhs])."""
-        nrhs = self._nrhs(B)
+        complex128 ([shift][rhs][...]); full-lattice vectors also in even-odd
+        mode, where each shift is solved through its Schur system.  Returns
+        (status, stats [shift][rhs])."""
+        # full-lattice vectors in both modes (even-odd: solved through A_hat)
+        if _numel(B) % self.n:
+            raise ValueError("B must hold whole full-lattice vectors")
+        nrhs = _numel(B) // self.n
         ns = len(mus)
         if _numel(X) != ns * _numel(B):
             raise ValueError("X must hold len(mus) * nrhs vectors")

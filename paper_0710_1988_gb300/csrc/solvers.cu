@@ -390,53 +390,91 @@ int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, doubl
 // (Sec. 4).  Before shift i, every right-hand side is projected over its own
 // solutions of shifts 0..i-1: with Q = [x_0 .. x_{i-1}], solve
 // Q^dagger A_i^dagger A_i Q d = Q^dagger A_i^dagger b and start from Q d.
+//
+// One shift: B (nrhs vectors of the handle's operator) and X, the solutions
+// of all shifts ([shift][rhs][n]); shift i's slot is written.
+namespace {
+struct ShiftWork {
+  double2 *R0, *Qc, *AQ, *part, *M, *c;
+  int *piv;
+  double *info;
+};
+}  // namespace
+
+static int shift_step(wd_context *h, const double2 *B, double2 *X, int i, int nrhs, double tol,
+                      int max_iter, int project, int mixed, wd_stats *st, cudaStream_t s,
+                      Arena &ar, const ShiftWork &w) {
+  const long long n = op_n(h);
+  double2 *R0 = w.R0, *Qc = w.Qc, *AQ = w.AQ, *part = w.part, *M = w.M, *c = w.c;
+  double2 *Xi = X + (size_t)i * nrhs * n;
+  WD_CK(cudaMemcpyAsync(R0, B, sizeof(double2) * nrhs * n, cudaMemcpyDeviceToDevice, s));
+  WD_CK(cudaMemsetAsync(Xi, 0, sizeof(double2) * nrhs * n, s));
+  if (st) std::memset(st, 0, sizeof(wd_stats) * nrhs);
+  if (project && i > 0) {
+    for (int r = 0; r < nrhs; ++r) {
+      for (int j = 0; j < i; ++j)
+        WD_CK(cudaMemcpyAsync(Qc + (size_t)j * n, X + ((size_t)j * nrhs + r) * n,
+                              sizeof(double2) * n, cudaMemcpyDeviceToDevice, s));
+      RET_IF(launch_ok(launch_wilson_f64(h, Qc, AQ, i, 0, s), "A Q"));
+      RET_IF(launch_ok(launch_ts_dot(AQ, i, AQ, i, 0, n, part, nullptr, s), "Q^H A^H A Q"));
+      RET_IF(launch_ok(launch_ts_dot_finalize(part, n, i, i, M, i, nullptr, 0, nullptr, s), "fin M"));
+      RET_IF(launch_ok(launch_ts_dot(AQ, i, B + (size_t)r * n, 1, 0, n, part, nullptr, s), "Q^H A^H b"));
+      RET_IF(launch_ok(launch_ts_dot_finalize(part, n, i, 1, c, 1, nullptr, 0, nullptr, s), "fin c"));
+      RET_IF(launch_ok(launch_lu_factor(M, i, w.piv, w.info, s), "lu"));
+      double hinfo[2];
+      WD_CK(cudaMemcpyAsync(hinfo, w.info, sizeof(hinfo), cudaMemcpyDeviceToHost, s));
+      WD_CK(cudaStreamSynchronize(s));
+      if (st) st[r].mvp_extra += i;
+      if (hinfo[0] != 0.0 || hinfo[1] > 1e14) continue;  // degenerate Q: start from 0
+      RET_IF(launch_ok(launch_lu_solve(M, w.piv, i, c, 1, s), "lu solve"));
+      RET_IF(launch_ok(launch_ts_update(Qc, i, c, 1, 1, nullptr, Xi + (size_t)r * n, 0, 1.0, n, nullptr, s), "x0 = Q d"));
+      RET_IF(launch_ok(launch_ts_update(AQ, i, c, 1, 1, B + (size_t)r * n, R0 + (size_t)r * n, 1, -1.0, n, nullptr, s), "r0 = b - A Q d"));
+    }
+  }
+  return mixed ? bicgstab_mixed_batched(h, B, Xi, R0, nrhs, tol, max_iter, 50, st, s, ar)
+               : bicgstab_batched(h, B, Xi, R0, nrhs, tol, max_iter, st, s, nullptr, 0, ar);
+}
+
+// In even-odd mode B and X are full-lattice vectors: each shift's source is
+// prepared with that shift's mu, the Schur system is solved (projected over
+// the earlier shifts' even-site solutions) and x_i is reconstructed.
 int tm_shifts_run(wd_context *h, const double2 *B, double2 *X, int nrhs, const double *mus,
                   int nshift, double tol, int max_iter, int project, int mixed,
                   wd_stats *stats, cudaStream_t s, Arena &ar) {
   const long long n = op_n(h);
   const double mu_saved = h->mu;
   const int kmax = nshift > 1 ? nshift - 1 : 1;
-  double2 *R0 = ar.take<double2>((size_t)nrhs * n);
-  double2 *Qc = ar.take<double2>((size_t)kmax * n);
-  double2 *AQ = ar.take<double2>((size_t)kmax * n);
-  double2 *part = ar.take<double2>(ts_dot_partial_count(n, kmax, kmax));
-  double2 *M = ar.take<double2>((size_t)kmax * kmax);
-  double2 *c = ar.take<double2>(kmax);
-  int *piv = ar.take<int>(kmax);
-  double *info = ar.take<double>(2);
+  ShiftWork w;
+  w.R0 = ar.take<double2>((size_t)nrhs * n);
+  w.Qc = ar.take<double2>((size_t)kmax * n);
+  w.AQ = ar.take<double2>((size_t)kmax * n);
+  w.part = ar.take<double2>(ts_dot_partial_count(n, kmax, kmax));
+  w.M = ar.take<double2>((size_t)kmax * kmax);
+  w.c = ar.take<double2>(kmax);
+  w.piv = ar.take<int>(kmax);
+  w.info = ar.take<double>(2);
+  const bool eo = h->eo != 0;
+  double2 *Bh = eo ? ar.take<double2>((size_t)nrhs * n) : nullptr;          // b_hat of the shift
+  double2 *Xh = eo ? ar.take<double2>((size_t)nshift * nrhs * n) : nullptr; // even solutions
+  double2 *be = eo ? ar.take<double2>((size_t)nrhs * n) : nullptr;
+  double2 *bo = eo ? ar.take<double2>((size_t)nrhs * n) : nullptr;
   if (ar.failed) return WD_OUT_OF_MEMORY;
   int rc = WD_OK;
   for (int i = 0; i < nshift && rc != WD_CUDA_ERROR && rc != WD_OUT_OF_MEMORY; ++i) {
     h->mu = mus[i];
-    double2 *Xi = X + (size_t)i * nrhs * n;
-    WD_CK(cudaMemcpyAsync(R0, B, sizeof(double2) * nrhs * n, cudaMemcpyDeviceToDevice, s));
-    WD_CK(cudaMemsetAsync(Xi, 0, sizeof(double2) * nrhs * n, s));
     wd_stats *st = stats ? stats + (size_t)i * nrhs : nullptr;
-    if (st) std::memset(st, 0, sizeof(wd_stats) * nrhs);
-    if (project && i > 0) {
-      for (int r = 0; r < nrhs; ++r) {
-        for (int j = 0; j < i; ++j)
-          WD_CK(cudaMemcpyAsync(Qc + (size_t)j * n, X + ((size_t)j * nrhs + r) * n,
-                                sizeof(double2) * n, cudaMemcpyDeviceToDevice, s));
-        RET_IF(launch_ok(launch_wilson_f64(h, Qc, AQ, i, 0, s), "A Q"));
-        RET_IF(launch_ok(launch_ts_dot(AQ, i, AQ, i, 0, n, part, nullptr, s), "Q^H A^H A Q"));
-        RET_IF(launch_ok(launch_ts_dot_finalize(part, n, i, i, M, i, nullptr, 0, nullptr, s), "fin M"));
-        RET_IF(launch_ok(launch_ts_dot(AQ, i, B + (size_t)r * n, 1, 0, n, part, nullptr, s), "Q^H A^H b"));
-        RET_IF(launch_ok(launch_ts_dot_finalize(part, n, i, 1, c, 1, nullptr, 0, nullptr, s), "fin c"));
-        RET_IF(launch_ok(launch_lu_factor(M, i, piv, info, s), "lu"));
-        double hinfo[2];
-        WD_CK(cudaMemcpyAsync(hinfo, info, sizeof(hinfo), cudaMemcpyDeviceToHost, s));
-        WD_CK(cudaStreamSynchronize(s));
-        if (st) st[r].mvp_extra += i;
-        if (hinfo[0] != 0.0 || hinfo[1] > 1e14) continue;  // degenerate Q: start from 0
-        RET_IF(launch_ok(launch_lu_solve(M, piv, i, c, 1, s), "lu solve"));
-        RET_IF(launch_ok(launch_ts_update(Qc, i, c, 1, 1, nullptr, Xi + (size_t)r * n, 0, 1.0, n, nullptr, s), "x0 = Q d"));
-        RET_IF(launch_ok(launch_ts_update(AQ, i, c, 1, 1, B + (size_t)r * n, R0 + (size_t)r * n, 1, -1.0, n, nullptr, s), "r0 = b - A Q d"));
-      }
+    int rci;
+    if (eo) {
+      RET_IF(launch_ok(launch_eo_prepare(h, B, Bh, be, bo, nrhs, s), "prepare"));
+      rci = shift_step(h, Bh, Xh, i, nrhs, tol, max_iter, project, mixed, st, s, ar, w);
+      if (rci != WD_CUDA_ERROR && rci != WD_OUT_OF_MEMORY && rci != WD_BAD_ARG)
+        RET_IF(launch_ok(launch_eo_reconstruct(h, B, Xh + (size_t)i * nrhs * n,
+                                               X + (size_t)i * nrhs * h->n, be, bo, nrhs, s),
+                         "reconstruct"));
+    } else {
+      rci = shift_step(h, B, X, i, nrhs, tol, max_iter, project, mixed, st, s, ar, w);
     }
-    int rci = mixed ? bicgstab_mixed_batched(h, B, Xi, R0, nrhs, tol, max_iter, 50, st, s, ar)
-                    : bicgstab_batched(h, B, Xi, R0, nrhs, tol, max_iter, st, s, nullptr, 0, ar);
-    if (rci == WD_CUDA_ERROR || rci == WD_OUT_OF_MEMORY) rc = rci;
+    if (rci == WD_CUDA_ERROR || rci == WD_OUT_OF_MEMORY || rci == WD_BAD_ARG) rc = rci;
     else if (rci != WD_OK && rc == WD_OK) rc = rci;
   }
   h->mu = mu_saved;
