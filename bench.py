@@ -542,6 +542,10 @@ def main():
 # FP32 / FP16 bytes per site and system of the mixed solver's kernels
 LOW_DSLASH_BYTES = {32: 3 * 96, 16: 52 + 52 + 96}   # in + out + (r_hat or r) per site update
 LOW_LINK_BYTES = {32: 4 * 48, 16: 4 * 24}            # links (rows 0, 1), read once per launch
+# even-odd Schur apply (FP32), per even site and system: v = A_hat p moves
+# SCHUR1 in + tmp and SCHUR2 tmp + p + out + r_hat; t = A_hat (r - alpha v) moves
+# SCHUR1 r + v + tmp and SCHUR2 tmp + r + v + out; the mean of the two applies
+LOW_SCHUR_BYTES = {32: (2 * 96 + 4 * 96 + 3 * 96 + 4 * 96) / 2}
 LOW_UPDATE_BYTES = {32: 4 * 96 + 8 * 96,             # p = r + beta (p - omega v); x, r update
                     16: (96 + 3 * 52) + (4 * 96 + 3 * 52 + 2 * 96)}
 
@@ -588,24 +592,34 @@ def timed_steps(args, step, op, flush, stream, world, dev, prof_mask=0):
     return ms_steps, last, prof, clocks.stop()
 
 
-def low_rooflines(prof, bits, V, peaks, iters_total):
+def low_rooflines(prof, bits, V, peaks, iters_total, eo=False):
     """HBM rooflines of the mixed solver's FP32/FP16 kernels from a profiled
     step: the Wilson apply (site updates counted on the device) and the two
-    per-iteration vector updates (one pass of each per system iteration)."""
+    per-iteration vector updates (one pass of each per system iteration).
+    On the even-odd Schur system (eo) one profiled launch is a Schur apply: two
+    half-lattice hop kernels, each reading every link, with V/2 counted site
+    updates per system (LOW_SCHUR_BYTES each); the vector updates run over V/2
+    sites."""
     hbm = peaks.get("hbm_gbs")
     out = {}
     d = prof["dslash_low"]
     if d["launches"]:
-        byt = LOW_DSLASH_BYTES[bits] * prof["dslash_low_site_updates"] + LOW_LINK_BYTES[bits] * V * d["launches"]
+        if eo:
+            byt = (LOW_SCHUR_BYTES[bits] * prof["dslash_low_site_updates"]
+                   + 2 * LOW_LINK_BYTES[bits] * V * d["launches"])
+        else:
+            byt = (LOW_DSLASH_BYTES[bits] * prof["dslash_low_site_updates"]
+                   + LOW_LINK_BYTES[bits] * V * d["launches"])
         gbs = byt / (d["ms"] * 1e-3) / 1e9
-        out["dslash"] = {"kernel": f"wilson_f{bits}_kernel", "bound": "hbm", "achieved": round(gbs, 1),
+        name = "wilson_eo32_kernel x2 (one Schur apply)" if eo else f"wilson_f{bits}_kernel"
+        out["dslash"] = {"kernel": name, "bound": "hbm", "achieved": round(gbs, 1),
                          "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4) if hbm else None,
                          "traffic": None, "avg_launch_ms": d["ms"] / d["launches"],
                          "launches": d["launches"],
                          "algorithmic_bytes_per_launch": byt / d["launches"]}
     u = prof["stream_low"]
     if u["launches"]:
-        byt = LOW_UPDATE_BYTES[bits] * V * iters_total
+        byt = LOW_UPDATE_BYTES[bits] * (V // 2 if eo else V) * iters_total
         gbs = byt / (u["ms"] * 1e-3) / 1e9
         out["updates"] = {"kernel": f"bicg{bits}_update_p + bicg{bits}_update_xr", "bound": "hbm",
                           "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
@@ -748,6 +762,8 @@ def twisted_arm(args, cfg, rank, world, local_rank):
     X = torch.zeros(len(mus) * cfg.n_rhs * n, dtype=torch.complex128, device=dev)
     op = wdl.WilsonOperator(cfg.dims, torch.from_numpy(U).to(dev), kappa)
     op.set_mixed_storage(args.storage)
+    if args.even_odd:  # each shift through its Schur system (Sec. 4 with even-odd)
+        op.set_operator(True)
     delta = 1e-3 if args.mixed_delta is None else args.mixed_delta
     op.set_mixed_restart(delta, 300)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
@@ -767,7 +783,8 @@ def twisted_arm(args, cfg, rank, world, local_rank):
     prof = op.profile_read()
     op.profile(mask=0)
     peaks = load_json(MEASURED_PEAKS, {}) or {}
-    roof = low_rooflines(prof, args.storage, v, peaks, sum(q["iters"] for row in sts_p for q in row))
+    roof = low_rooflines(prof, args.storage, v, peaks, sum(q["iters"] for row in sts_p for q in row),
+                         eo=args.even_odd)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -795,7 +812,9 @@ def twisted_arm(args, cfg, rank, world, local_rank):
     extra["gpu_launches"] = int(sum(c["launches"] for c in extra["kernel_breakdown_ms"].values()))
     return _row_line(cfg, args, world, units * args.steps * world / (total_ms * 1e-3), "solves/s",
                      total_ms, f"f{args.storage} iteration, f64 reliable updates",
-                     f"{cfg.name}: A_W + i mu gamma5 at kappa_c, shifts {mus} heaviest first, each "
+                     f"{cfg.name}: A_W + i mu gamma5 at kappa_c"
+                     + (" on the even-odd Schur system" if args.even_odd else "")
+                     + f", shifts {mus} heaviest first, each "
                      f"projected over the earlier solutions (Sec. 4), {cfg.n_rhs} Gaussian sources "
                      f"per shift batched, mixed BiCGStab (FP{args.storage}, "
                      + ("reliable updates every 50" if delta == 0 else

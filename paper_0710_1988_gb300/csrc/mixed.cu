@@ -125,8 +125,12 @@ __device__ __forceinline__ void hop32(const float4 *__restrict__ links, const fl
 
 // EPI_NONE: out = A in.   EPI_DOT: out = A in, partial <aux, out>, ||out||^2.
 // EPI_TSTT (FUSED): out = A s with s = in - alpha in2, partial <out, s>, ||out||^2.
+// R = 1 shapes are held to 80 registers (768 threads per SM, 6 blocks of 128):
+// the kernel waits on gathers, and the sixth block's warps hide more of that
+// latency than the few spilled words cost (0.778 -> 0.692 ms at 24^3 x 48
+// with 16 systems).
 template <int R, int TPB, bool DAG, int EPI, bool FUSED>
-__global__ void __launch_bounds__(TPB)
+__global__ void __launch_bounds__(TPB, R == 1 ? 768 / TPB : 1)
 wilson_f32_kernel(const float4 *__restrict__ links, const float4 *__restrict__ in,
                   const float4 *__restrict__ in2, float4 *__restrict__ out, LatticeGeom g,
                   float kappa, float mu, int nrhs, const BicgScalars *__restrict__ sc,

@@ -117,23 +117,29 @@ enum { EO32_SCHUR1 = 0, EO32_SCHUR2 = 1 };
 // FUSED: the even operand is s = r - alpha v, read from (src, src2) in
 // SCHUR1 and from (same, same2) in SCHUR2.
 template <bool DAG, int MODE, int EPI, bool FUSED>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 6)  // 80 registers, as the full FP32 kernel
 wilson_eo32_kernel(const float4 *__restrict__ links, const float4 *__restrict__ src,
                    const float4 *__restrict__ src2, const float4 *__restrict__ same,
                    const float4 *__restrict__ same2, float4 *__restrict__ out, LatticeGeom g,
                    int pout, float kappa, float mu, const BicgScalars *__restrict__ sc,
                    const float4 *__restrict__ aux, double *__restrict__ partial,
                    const int *__restrict__ status, unsigned mask,
-                   unsigned long long *__restrict__ sites) {
-  const int r = blockIdx.y;
+                   unsigned long long *__restrict__ sites, int nrhs) {
+  // Blocks are numbered system fastest: the nrhs blocks that cover one range
+  // of sites run side by side and share the links through L2, which a
+  // half-lattice hop reads in full (every link touches one site of each
+  // parity).
+  const int r = (int)(blockIdx.x % (unsigned)nrhs);
+  const long long sb = blockIdx.x / (unsigned)nrhs;  // site block
+  const long long nsb = gridDim.x / (unsigned)nrhs;
   if (status != nullptr && !((mask >> status[r]) & 1u)) return;  // uniform per block
   const long long V = g.V, Vh = g.V / 2;
-  if (sites != nullptr && blockIdx.x == 0 && threadIdx.x == 0)
+  if (sites != nullptr && sb == 0 && threadIdx.x == 0)
     atomicAdd(sites, (unsigned long long)Vh);  // work accounting for the profiler
   const float2 alpha = FUSED ? make_float2((float)sc[r].alpha.x, (float)sc[r].alpha.y)
                              : make_float2(0.f, 0.f);
   const long long off = (long long)r * 6 * Vh;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long i = sb * blockDim.x + threadIdx.x;
   float red[3] = {0.f, 0.f, 0.f};
   if (i < Vh) {
     // the site of parity pout in the x-pair (2i, 2i + 1)
@@ -219,7 +225,7 @@ wilson_eo32_kernel(const float4 *__restrict__ links, const float4 *__restrict__ 
     }
     __syncthreads();
     if (threadIdx.x < 3)
-      partial[((long long)r * gridDim.x + blockIdx.x) * 3 + threadIdx.x] =
+      partial[((long long)r * nsb + sb) * 3 + threadIdx.x] =
           ((sh[threadIdx.x][0] + sh[threadIdx.x][1]) + sh[threadIdx.x][2]) + sh[threadIdx.x][3];
   }
 }
@@ -236,13 +242,13 @@ cudaError_t launch_schur_f32(const Mixed32 &m, const float4 *in, const float4 *i
   ProfLaunch prof(PC_DSLASH_LOW, s);
   const wd_context *h = m.h;
   const LatticeGeom g = geom_of(h);
-  const dim3 grid((unsigned)schur32_blocks(h), nrhs);
+  const dim3 grid((unsigned)schur32_blocks(h) * (unsigned)nrhs);
   const float kap = (float)h->kappa, mu = (float)h->mu;
   unsigned long long *cnt = prof_site_counter_low();
 #define EO32(D, M, E, FU, SRC, SRC2, SAME, SAME2, OUT, POUT, CNT)                               \
   wilson_eo32_kernel<D, M, E, FU><<<grid, 128, 0, s>>>(m.links, SRC, SRC2, SAME, SAME2, OUT, g, \
                                                        POUT, kap, mu, sc, aux, partial, status, \
-                                                       mask, CNT)
+                                                       mask, CNT, nrhs)
   if (epi == EPI_TSTT) {
     EO32(false, EO32_SCHUR1, EPI_NONE, true, in, in2, nullptr, nullptr, tmp, 1, nullptr);
     EO32(false, EO32_SCHUR2, EPI_TSTT, true, tmp, nullptr, in, in2, out, 0, cnt);

@@ -1,6 +1,7 @@
 """Run one Wilson-operator kernel on its own, for profilers and timing.
 
     python -m paper_0710_1988_gb300.kernel_case --kernel f32 --lattice 20 20 20 32 --nrhs 12
+    python -m paper_0710_1988_gb300.kernel_case --kernel f32 --even-odd --lattice 24 24 24 48 --nrhs 16
 
 Builds a seeded gauge field (U = exp(i 0.5 H)) and Gaussian spinors, then
 applies the operator `--reps` times through the public binding (`apply`,
@@ -30,19 +31,35 @@ def main(argv=None):
     ap.add_argument("--nrhs", type=int, default=12)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--kappa", type=float, default=0.14)
+    ap.add_argument("--storage", type=int, choices=[32, 16], default=32,
+                    help="vector storage of the mixed solver (--kernel mixed)")
+    ap.add_argument("--even-odd", action="store_true",
+                    help="the even-odd Schur operator on even half vectors (f64 and f32 only)")
     args = ap.parse_args(argv)
     dims = tuple(args.lattice)
     U = L.gauge_field(dims, 0.5, 1002)
-    psi = L.gaussian_spinor(dims, 2200, nrhs=args.nrhs).reshape(-1)
+    psi = L.gaussian_spinor(dims, 2200, nrhs=args.nrhs)
     op = wdl.WilsonOperator(dims, torch.from_numpy(U).cuda(), args.kappa)
-    x = torch.from_numpy(psi).cuda()
+    if args.even_odd:
+        op.set_operator(True)
+        psi = psi.reshape(args.nrhs, -1)[:, : op.op_n]  # any values serve as even half vectors
+    x = torch.from_numpy(np.ascontiguousarray(psi).reshape(-1)).cuda()
     y = torch.empty_like(x)
     if args.kernel == "mixed":
+        op.set_mixed_storage(args.storage)
         y.zero_()
+        op.dbicgstab_mixed(x, y, None, tol=1e-30, max_iter=3)  # warm-up (graphs, tuning)
+        y.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
         rc, sts = op.dbicgstab_mixed(x, y, None, tol=1e-30, max_iter=args.reps)
+        e1.record()
         torch.cuda.synchronize()
         print(json.dumps({"kernel": "mixed", "lattice": list(dims), "nrhs": args.nrhs,
-                          "iters": [q["iters"] for q in sts], "status": rc}))
+                          "even_odd": args.even_odd, "storage": args.storage,
+                          "iters": [q["iters"] for q in sts][:4],
+                          "ms": e0.elapsed_time(e1), "status": rc}))
         op.close()
         return
     fn = {"f64": op.apply, "f32": op.apply_f32, "f16": op.apply_f16}[args.kernel]
@@ -57,7 +74,7 @@ def main(argv=None):
     cat = "dslash" if args.kernel == "f64" else "dslash_low"
     ms = p[cat]["ms"] / max(1, p[cat]["launches"])
     print(json.dumps({"kernel": args.kernel, "lattice": list(dims), "nrhs": args.nrhs,
-                      "ms_per_apply": ms, "finite": bool(np.isfinite(y.abs().max().item()))}))
+                      "even_odd": args.even_odd, "ms_per_apply": ms, "finite": bool(np.isfinite(y.abs().max().item()))}))
     op.close()
 
 
