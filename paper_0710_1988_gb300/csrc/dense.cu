@@ -21,6 +21,7 @@ namespace wd {
 constexpr int LU_THREADS = 256;
 constexpr int CE_THREADS = 256;
 constexpr int CE_MAXM = 80;
+static_assert(CE_THREADS > CE_MAXM, "the least-squares step gives one thread to each column and one more to the right-hand side");
 
 // shared-memory leading dimension of an m-column complex matrix: the next
 // value = 1 (mod 8) at or above m
@@ -228,32 +229,28 @@ cudaError_t launch_lu_solve(const double2 *LU, const int *piv, int k, double2 *C
 
 // ----------------------------------------------------------------- GMRES-DR cycle end
 
-// Apply the Householder reflector I - tau u u^dagger (u[i] for i >= i0) from
-// the left to columns [c0, c1) of X (rows i0..i1, leading dim ld), one warp
-// per column.
-__device__ void reflect_left(double2 *X, int ld, const double2 *u, double tau, int i0, int i1,
-                             int c0, int c1) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int c = c0 + w; c < c1; c += nw) {
+// One thread per line (column of X from the left, row of Y from the right):
+// the left reflection on columns [c0, c1) of X and, in the same pass, the
+// right reflection on rows [0, ny) of Y, both over indices i0..i1.  Each
+// thread forms its own dot product serially, so every lane of an FP64
+// instruction does useful work and no cross-lane reduction is needed; the
+// reflector's support is short (i1 - i0 < k + 1 after a restart).
+__device__ void reflect_lines(double2 *X, int c0, int c1, double2 *Y, int ny, int ld,
+                              const double2 *u, double tau, int i0, int i1) {
+  const int nx = X != nullptr ? c1 - c0 : 0;
+  for (int t = threadIdx.x; t < nx + ny; t += blockDim.x) {
     double2 s = make_double2(0.0, 0.0);
-    for (int i = i0 + lane; i <= i1; i += 32) s = cfmac(u[i], X[i * ld + c], s);
-    s = warp_csum_all(s);
-    const double2 f = cscale(tau, s);
-    for (int i = i0 + lane; i <= i1; i += 32) X[i * ld + c] = csub(X[i * ld + c], cmul(u[i], f));
-  }
-}
-
-// ... and from the right to rows [r0, r1) of X (columns i0..i1).
-__device__ void reflect_right(double2 *X, int ld, const double2 *u, double tau, int i0, int i1,
-                              int r0, int r1) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int r = r0 + w; r < r1; r += nw) {
-    double2 s = make_double2(0.0, 0.0);
-    for (int i = i0 + lane; i <= i1; i += 32) s = cfma(X[r * ld + i], u[i], s);
-    s = warp_csum_all(s);
-    const double2 f = cscale(tau, s);
-    for (int i = i0 + lane; i <= i1; i += 32)
-      X[r * ld + i] = csub(X[r * ld + i], cmul(f, cconj(u[i])));
+    if (t < nx) {  // X <- (I - tau u u^dagger) X, column c
+      const int c = c0 + t;
+      for (int i = i0; i <= i1; ++i) s = cfmac(u[i], X[i * ld + c], s);
+      const double2 f = cscale(tau, s);
+      for (int i = i0; i <= i1; ++i) X[i * ld + c] = csub(X[i * ld + c], cmul(u[i], f));
+    } else {       // Y <- Y (I - tau u u^dagger), row r
+      const int r = t - nx;
+      for (int i = i0; i <= i1; ++i) s = cfma(Y[r * ld + i], u[i], s);
+      const double2 f = cscale(tau, s);
+      for (int i = i0; i <= i1; ++i) Y[r * ld + i] = csub(Y[r * ld + i], cmul(f, cconj(u[i])));
+    }
   }
 }
 
@@ -268,24 +265,51 @@ __device__ void cycle_lsq(const CycleEndArgs &a, int me, double2 *sm) {
   double2 *dd = u + (m + 1);           // m
   for (int e = threadIdx.x; e < (m + 1) * m; e += blockDim.x) Hs[(e / m) * ld + e % m] = a.H[e];
   for (int i = threadIdx.x; i <= m; i += blockDim.x) cz[i] = a.c[i];
+  // Each reflector spans rows j .. iend, iend the last nonzero row of column
+  // j (j + 1 in the Hessenberg part, k after a restart in the leading full
+  // block): a shared atomic maximum, triple-buffered as in schur_block so that
+  // no slot is reset while another thread may still read or update it.
+  __shared__ int s_end[3];
+  if (threadIdx.x < 3) s_end[threadIdx.x] = 0;
   __syncthreads();
   for (int j = 0; j < me; ++j) {
+    const int slot = j % 3;
     double part = 0.0;
-    for (int i = j + threadIdx.x; i <= me; i += blockDim.x) part += cnorm2(Hs[i * ld + j]);
-    const double sigma = block_dsum_all(part);
+    for (int i = j + threadIdx.x; i <= me; i += blockDim.x) {
+      const double2 h = Hs[i * ld + j];
+      part += cnorm2(h);
+      if (h.x != 0.0 || h.y != 0.0) atomicMax(&s_end[slot], i);
+    }
+    const double sigma = block_dsum_all(part);  // its barriers order the atomics
+    const int iend = s_end[slot];
+    if (threadIdx.x == 0) s_end[(j + 2) % 3] = 0;
     if (sigma == 0.0) continue;
     const double2 al = Hs[j * ld + j];
     const double nx = sqrt(sigma), aa = cabs_(al);
     const double2 ph = aa > 0.0 ? cscale(1.0 / aa, al) : make_double2(1.0, 0.0);
     const double2 beta = cscale(-nx, ph);
-    for (int i = j + threadIdx.x; i <= me; i += blockDim.x)
+    for (int i = j + threadIdx.x; i <= iend; i += blockDim.x)
       u[i] = i == j ? csub(al, beta) : Hs[i * ld + j];
     __syncthreads();
     const double tau = 1.0 / (nx * (nx + aa));  // 2 / ||u||^2
-    reflect_left(Hs, ld, u, tau, j, me, j + 1, me);
-    reflect_left(cz, 1, u, tau, j, me, 0, 1);
+    // columns j+1 .. me-1 of Hbar (threads 0 .. me-j-2) and the right-hand
+    // side (the last thread; blockDim.x > CE_MAXM keeps the two apart)
+    double2 *col = nullptr;
+    int cld = ld;
+    if (threadIdx.x == blockDim.x - 1) {
+      col = cz;
+      cld = 1;
+    } else if (threadIdx.x < me - j - 1) {
+      col = Hs + j + 1 + threadIdx.x;
+    }
+    if (col != nullptr) {
+      double2 sd = make_double2(0.0, 0.0);
+      for (int i = j; i <= iend; ++i) sd = cfmac(u[i], col[i * cld], sd);
+      const double2 f = cscale(tau, sd);
+      for (int i = j; i <= iend; ++i) col[i * cld] = csub(col[i * cld], cmul(u[i], f));
+    }
     __syncthreads();
-    for (int i = j + threadIdx.x; i <= me; i += blockDim.x)
+    for (int i = j + threadIdx.x; i <= iend; i += blockDim.x)
       Hs[i * ld + j] = i == j ? beta : make_double2(0.0, 0.0);
     __syncthreads();
   }
@@ -325,6 +349,39 @@ __device__ __forceinline__ void givens(double2 x, double2 y, double &c, double2 
   s = cscale(ra * rn, cmul(x, cconj(y)));
 }
 
+// givens() computed by one warp (x, y the same on every lane; every lane
+// calls it).  An FP64 instruction occupies the warp's pipe as long with one
+// active lane as with 32, so the independent products go to separate lanes:
+// lane 0 |x|^2, lane 1 |y|^2, lane 2 and 3 Re and Im of x conj(y), then one
+// rsqrt (lane 0 of |x|^2, the others of |x|^2 + |y|^2) and two multiplies
+// (lane 0 c, lanes 2 and 3 s).  Each value is rounded exactly as in givens().
+// Lane 0 writes c and s.
+__device__ __forceinline__ void givens_lanes(double2 x, double2 y, int ln, double *gc,
+                                             double2 *gs) {
+  const double f0 = ln == 1 ? y.x : x.x;
+  const double f1 = ln == 0 ? x.x : (ln == 3 ? -y.y : y.x);
+  const double f2 = ln == 1 ? y.y : x.y;
+  const double f3 = ln == 0 ? x.y : (ln == 3 ? y.x : y.y);
+  const double q = fma(f0, f1, f2 * f3);
+  const double a2 = __shfl_sync(0xffffffffu, q, 0), b2 = __shfl_sync(0xffffffffu, q, 1);
+  if (a2 == 0.0) {  // uniform over the warp
+    if (ln == 0) {
+      *gc = 0.0;
+      *gs = make_double2(1.0, 0.0);
+    }
+    return;
+  }
+  const double r = rsqrt(ln == 0 ? a2 : a2 + b2);
+  const double ra = __shfl_sync(0xffffffffu, r, 0), rn = __shfl_sync(0xffffffffu, r, 1);
+  const double t = ln == 0 ? a2 * ra : ra * rn;
+  const double u = ln == 0 ? t * rn : t * q;
+  const double sx = __shfl_sync(0xffffffffu, u, 2), sy = __shfl_sync(0xffffffffu, u, 3);
+  if (ln == 0) {
+    *gc = u;
+    *gs = make_double2(sx, sy);
+  }
+}
+
 // Schur decomposition of the m x m matrix A (smem, row-major): on return
 // A holds upper triangular T and Z the unitary Schur vectors, A_in = Z T Z^dagger.
 // Returns 1 if the QR iteration did not converge in 30 m sweeps.
@@ -361,10 +418,10 @@ __device__ int schur_block(double2 *A, double2 *Z, int m, int ld, double2 *u, lo
     for (int i = j + 1 + tid; i <= iend; i += bd) u[i] = i == j + 1 ? csub(al, beta) : A[i * ld + j];
     __syncthreads();
     const double tau = 1.0 / (nx * (nx + aa));
-    reflect_left(A, ld, u, tau, j + 1, iend, j, m);
+    // H A on columns j..m-1 together with Z H (independent of A), then A H
+    reflect_lines(A, j, m, Z, m, ld, u, tau, j + 1, iend);
     __syncthreads();
-    reflect_right(A, ld, u, tau, j + 1, iend, 0, m);
-    reflect_right(Z, ld, u, tau, j + 1, iend, 0, m);
+    reflect_lines(nullptr, 0, 0, A, m, ld, u, tau, j + 1, iend);
     __syncthreads();
     for (int i = j + 1 + tid; i <= iend; i += bd)
       A[i * ld + j] = i == j + 1 ? beta : make_double2(0.0, 0.0);
@@ -463,8 +520,8 @@ __device__ int schur_block(double2 *A, double2 *Z, int m, int ld, double2 *u, lo
         // lane (an FP64 instruction occupies the warp's pipe for the same time
         // whether 1 or 32 lanes are active, so serial work is spread over
         // lanes).  Lanes 0..3: row rotation on the 2 x 2 block (kk, kk+1)^2;
-        // then lanes 0..5: column rotation on rows kk..kk+2; then lane 0
-        // forms the next rotation from column kk.
+        // then lanes 0..5: column rotation on rows kk..kk+2; then lanes 0..3
+        // form the next rotation from column kk.
         const int ln = tid - rt;
         double2 v = make_double2(0.0, 0.0);
         if (ln < 4) {
@@ -488,7 +545,7 @@ __device__ int schur_block(double2 *A, double2 *Z, int m, int ld, double2 *u, lo
         x.y = __shfl_sync(0xffffffffu, o.y, 2);
         y.x = __shfl_sync(0xffffffffu, o.x, 4);
         y.y = __shfl_sync(0xffffffffu, o.y, 4);
-        if (ln == 0 && kk + 1 < hi) givens(x, y, s_gc[kk + 1], s_gs[kk + 1]);
+        if (kk + 1 < hi) givens_lanes(x, y, ln, &s_gc[kk + 1], &s_gs[kk + 1]);
       } else {
         // Everything else of rotation kk, concurrently, on the other seven
         // warps; warps 0-2 and 4-6 take the first 192 entries and warp 3
