@@ -34,11 +34,19 @@ bicg_update_p_kernel(double2 *__restrict__ p, const double2 *__restrict__ rv,
                      const double2 *__restrict__ vv, const BicgScalars *__restrict__ sc,
                      const int *__restrict__ status, long long n) {
   const int r = blockIdx.y;
-  if (!sys_on(status, M_ACTIVE, r)) return;
-  const BicgScalars S = sc[r];
-  // beta = (rho / rho_old) (alpha / omega)
-  const double2 beta = cmul(cdiv(S.rho, S.rho_old), cdiv(S.alpha, S.omega));
-  const double2 mbo = cneg(cmul(beta, S.omega));
+  if (!sys_on(status, M_ACTIVE, r)) return;  // uniform per block
+  // beta = (rho / rho_old) (alpha / omega), once per block: two complex
+  // divisions in every thread cost more FP64 issue than the few elements
+  // each thread updates
+  __shared__ double2 s_bm[2];
+  if (threadIdx.x == 0) {
+    const BicgScalars S = sc[r];
+    const double2 beta = cmul(cdiv(S.rho, S.rho_old), cdiv(S.alpha, S.omega));
+    s_bm[0] = beta;
+    s_bm[1] = cneg(cmul(beta, S.omega));
+  }
+  __syncthreads();
+  const double2 beta = s_bm[0], mbo = s_bm[1];
   const long long off = (long long)r * n;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
@@ -570,8 +578,11 @@ __global__ void scale_by_inverse_entry_kernel(double2 *__restrict__ v,
                                               const double2 *__restrict__ w,
                                               const double2 *__restrict__ H, int idx,
                                               long long n, const int *__restrict__ status) {
-  if (status != nullptr && *status != 0) return;
-  const double inv = 1.0 / H[idx].x;
+  if (status != nullptr && *status != 0) return;  // uniform over the grid
+  __shared__ double s_inv;  // one division per block, not per thread
+  if (threadIdx.x == 0) s_inv = 1.0 / H[idx].x;
+  __syncthreads();
+  const double inv = s_inv;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     v[i] = cscale(inv, w[i]);

@@ -519,10 +519,16 @@ bicg32_update_p_kernel(float4 *__restrict__ p, const float4 *__restrict__ r,
                        const float4 *__restrict__ v, const BicgScalars *__restrict__ sc,
                        const int *__restrict__ status, long long n4) {
   const int q = blockIdx.y;
-  if (!on32(status, M_ACTIVE, q)) return;
-  const BicgScalars S = sc[q];
-  const double2 bd = cmul(cdiv(S.rho, S.rho_old), cdiv(S.alpha, S.omega));
-  const float2 beta = f2(bd), mom = make_float2(-(float)S.omega.x, -(float)S.omega.y);
+  if (!on32(status, M_ACTIVE, q)) return;  // uniform per block
+  // beta in FP64 once per block (as in bicg_update_p_kernel)
+  __shared__ float2 s_bm[2];
+  if (threadIdx.x == 0) {
+    const BicgScalars S = sc[q];
+    s_bm[0] = f2(cmul(cdiv(S.rho, S.rho_old), cdiv(S.alpha, S.omega)));
+    s_bm[1] = make_float2(-(float)S.omega.x, -(float)S.omega.y);
+  }
+  __syncthreads();
+  const float2 beta = s_bm[0], mom = s_bm[1];
   const long long off = (long long)q * n4;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
        i += (long long)gridDim.x * blockDim.x) {

@@ -486,10 +486,16 @@ bicg16_update_p_kernel(Half16 p, const float4 *__restrict__ r, Half16 v,
                        const BicgScalars *__restrict__ sc, const int *__restrict__ status,
                        long long V) {
   const int q = blockIdx.y;
-  if (!on16(status, M_ACTIVE, q)) return;
-  const BicgScalars S = sc[q];
-  const float2 beta = f2of(cmul(cdiv(S.rho, S.rho_old), cdiv(S.alpha, S.omega)));
-  const float2 mom = make_float2(-(float)S.omega.x, -(float)S.omega.y);
+  if (!on16(status, M_ACTIVE, q)) return;  // uniform per block
+  // beta in FP64 once per block (as in bicg_update_p_kernel)
+  __shared__ float2 s_bm[2];
+  if (threadIdx.x == 0) {
+    const BicgScalars S = sc[q];
+    s_bm[0] = f2of(cmul(cdiv(S.rho, S.rho_old), cdiv(S.alpha, S.omega)));
+    s_bm[1] = make_float2(-(float)S.omega.x, -(float)S.omega.y);
+  }
+  __syncthreads();
+  const float2 beta = s_bm[0], mom = s_bm[1];
   for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < V;
        s += (long long)gridDim.x * blockDim.x) {
     float2 rv[12], pv[12], vv[12];
