@@ -445,13 +445,12 @@ __device__ int schur_block(double2 *A, double2 *Z, int m, int ld, double2 *u, lo
   }
   const double anorm = part > 0.0 ? part : 1.0;
   if (clk != nullptr && tid == 0) clk[7] = clock64();
-  // Shifted QR iteration.  Within a sweep only the active block
-  // [l..hi] x [l..hi] is updated rotation by rotation, one barrier per
-  // rotation.  Lane 0 of the last warp (rt) computes the shift and every
+  // Shifted QR iteration, one barrier per rotation of a sweep over the
+  // active block [l..hi].  The last warp (rt) computes the shift and every
   // rotation and applies each rotation to the few entries the next one
-  // depends on; the other warps apply it everywhere else at the same time.
-  // The parts of T outside the active block and the Schur vectors Z receive
-  // the sweep's rotations afterwards, one thread per row or column.
+  // depends on; the other warps apply it, in the same barrier interval,
+  // everywhere else: the rest of the active block, the parts of T outside it
+  // and the Schur vectors Z.
   __shared__ double s_gc[CE_MAXM];
   __shared__ double2 s_gs[CE_MAXM];
   __shared__ int s_l[2];    // deflation point of the scan, double-buffered

@@ -302,7 +302,7 @@ int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, doubl
       std::fprintf(stderr,
                    "cycle_end clk: lsq %lld lu %lld hessenberg %lld qr-iter %lld eigvec %lld "
                    "qr(P) %lld products %lld | sweeps %lld rotations %lld scan %lld rot %lld "
-                   "deferred %lld\n",
+                   "tail %lld\n",
                    hc[1] - hc[0], hc[2] - hc[1], hc[7] - hc[2], hc[3] - hc[7], hc[4] - hc[3],
                    hc[5] - hc[4], hc[6] - hc[5], hc[8], hc[9], hc[10], hc[11], hc[12]);
     }
