@@ -1,7 +1,7 @@
 """Critical hopping parameter kappa_c (oracle).
 
-Sec. 3 fixes kappa_c on each configuration as the kappa at which the real
-part of the smallest eigenvalue of A vanishes.  Every eigenvalue of
+Sec. 3 defines kappa_c per gauge configuration: the kappa at which the
+leftmost eigenvalue of A reaches the imaginary axis.  Every eigenvalue of
 A = 1 - kappa*D is 1 - kappa*lambda with lambda an eigenvalue of D, so for
 kappa > 0 the smallest real part is 1 - kappa*max Re lambda(D) and
 
