@@ -2,9 +2,9 @@
  * wd.h - C ABI of the GB300 deflated-BiCGStab library (libwd.so).
  *
  * Method: Abdel-Rehim, Morgan, Wilcox, "Deflated BiCGStab for linear
- * equations in QCD problems" (Lattice 2007).  The first right-hand side is
- * solved by GMRES-DR(m,k), which also yields k approximate right
- * eigenvectors V (Sec. 1).  Every later right-hand side gets the k x k
+ * equations in QCD problems" (Lattice 2007).  GMRES-DR(m,k) takes the
+ * first right-hand side and also yields k approximate right eigenvectors
+ * V (Sec. 1).  Every later right-hand side gets the k x k
  * left-right projection (U^dagger A V) y = U^dagger r0, x0 += V y, with
  * U = gamma5 V from gamma5 A gamma5 = A^dagger, and then plain BiCGStab
  * (Sec. 2).
