@@ -51,6 +51,7 @@ class SolveStats:
     rel_res: float = np.inf   # recursive (or least-squares) residual / ||b||
     true_rel_res: float = np.inf
     history: List[float] = field(default_factory=list)
+    x0: Optional[np.ndarray] = None   # starting guess after a projection (Sec. 2, 4)
 
 
 def _norm(x):
@@ -311,9 +312,11 @@ def dbicgstab(apply: Apply, b: np.ndarray, V: np.ndarray,
         x = x + V.T @ y
         r0 = b - apply(x)
         extra += 1
+    x0_proj = x.copy()
     x, st = bicgstab(apply, b, x0=x, tol=tol, max_iter=max_iter, r0=r0,
                      bnorm=_norm(b))
     st.mvp_extra += extra
+    st.x0 = x0_proj
     return x, st
 
 
@@ -347,6 +350,7 @@ def serial_shifts(apply_mu: Callable[[float], Apply], b: np.ndarray, mus,
         x, st = bicgstab(apply, b, x0=x0, tol=tol, max_iter=max_iter, r0=r0,
                          bnorm=_norm(b))
         st.mvp_extra += extra
+        st.x0 = x0
         xs.append(x)
         stats.append(st)
     return xs, stats

@@ -483,6 +483,111 @@ def test_serial_shift_projection_cuts_work():
     assert sum(s.mvp for s in st1) < sum(s.mvp for s in st0)
 
 
+def _dense_gamma5(v):
+    """gamma5 = diag(1, 1, -1, -1) on spin, identity on site and colour, built
+    as a dense n x n matrix (independent of dirac.gamma5)."""
+    return np.kron(np.eye(v), np.kron(np.diag([1.0, 1.0, -1.0, -1.0]), np.eye(3))).astype(complex)
+
+
+def _exact_right_eigvecs(Ad, k):
+    lam, W = np.linalg.eig(Ad)
+    idx = np.argsort(np.abs(lam))[:k]
+    Q, _ = np.linalg.qr(W[:, idx])
+    return Q.T, lam[idx]
+
+
+@pytest.mark.parametrize("basis", ["gmresdr", "exact"])
+def test_dbicgstab_starts_from_the_left_right_projection(small_system, basis):
+    """Sec. 2: before BiCGStab, x0 = V y with (U^H A V) y = U^H b and U =
+    gamma5 V.  With max_iter = 0 the oracle returns that x0; it must equal
+    the projection computed here from the dense matrix and an explicitly
+    built gamma5, and satisfy the Petrov-Galerkin condition for gamma5 V
+    (a default U = V, or a projection on the wrong residual, fails both)."""
+    s = small_system
+    k = 6
+    if basis == "gmresdr":
+        V = krylov.gmresdr(s["A"], s["b"], m=20, k=k, tol=1e-12).V
+    else:
+        V, _ = _exact_right_eigvecs(s["Ad"], k)
+    n = s["b"].size
+    G5 = _dense_gamma5(n // 12)
+    Vc = V.T                                     # n x k, columns
+    U = G5 @ Vc
+    b2 = _vec(s["dims"], 88).ravel()
+    G = U.conj().T @ s["Ad"] @ Vc
+    y = np.linalg.solve(G, U.conj().T @ b2)
+    x_ref = Vc @ y
+    x, st = krylov.dbicgstab(s["A"], b2, V, tol=1e-12, max_iter=0, gamma5=s["g5"])
+    assert st.iters == 0 and st.mvp == 0
+    # G = (gamma5 V)^H A V is Hermitian indefinite and can be ill-conditioned:
+    # two LU solves agree to a few ulps times cond(G)
+    assert np.linalg.norm(x - x_ref) <= 64 * np.linalg.cond(G) * 2.2e-16 * np.linalg.norm(x_ref)
+    assert np.array_equal(st.x0, x)
+    assert np.abs(U.conj().T @ (b2 - s["Ad"] @ x)).max() <= 1e-12 * np.linalg.norm(b2)
+
+
+def test_dbicgstab_iterates_on_the_projected_residual(small_system):
+    """After one BiCGStab iteration from the projected x0 the recursive
+    residual equals the true residual b - A x (exact in arithmetic), and, with
+    exact right eigenvectors, that residual stays orthogonal to the k left
+    eigenvectors of the same eigenvalues (A maps their orthogonal complement
+    into itself).  A stale residual handed to BiCGStab breaks both."""
+    s = small_system
+    k = 4
+    V, lam = _exact_right_eigvecs(s["Ad"], k)
+    b2 = _vec(s["dims"], 89).ravel()
+    x1, st = krylov.dbicgstab(s["A"], b2, V, tol=1e-14, max_iter=1, gamma5=s["g5"])
+    assert st.iters == 1 and st.mvp == 2 and len(st.history) == 1
+    r_true = np.linalg.norm(b2 - s["Ad"] @ x1) / np.linalg.norm(b2)
+    assert abs(st.history[0] - r_true) <= 1e-10 * r_true
+    lamL, WL = np.linalg.eig(s["Ad"].conj().T)
+    r1 = b2 - s["Ad"] @ x1
+    for l in lam:
+        j = np.argmin(np.abs(lamL - np.conj(l)))
+        assert abs(np.vdot(WL[:, j], r1)) <= 1e-10 * np.linalg.norm(b2)
+
+
+def test_dbicgstab_solution_matches_lu(small_system):
+    s = small_system
+    V = krylov.gmresdr(s["A"], s["b"], m=20, k=6, tol=1e-12).V
+    b2 = _vec(s["dims"], 90).ravel()
+    x, st = krylov.dbicgstab(s["A"], b2, V, tol=1e-12, gamma5=s["g5"])
+    assert st.converged and st.mvp % 2 == 0 and st.true_rel_res <= 1e-12
+    xs = np.linalg.solve(s["Ad"], b2)
+    assert np.linalg.norm(x - xs) <= 2 * s["cond"] * 1e-12 * np.linalg.norm(xs)
+
+
+def test_serial_shifts_start_from_least_squares_over_previous_solutions():
+    """Sec. 4: shift i starts from x0 = Q d with d = argmin ||b - A(mu_i) Q d||
+    over the solutions Q of the shifts already solved.  Checked against
+    lstsq on the dense A(mu_i) = A_W + i mu_i gamma5 assembled here (the
+    operator of the previous shift, or no projection, fails)."""
+    dims = (2, 2, 2, 4)
+    U = L.gauge_field(dims, 0.5, 97)
+    kap = 0.13
+    v = U.shape[0]
+    Aw = _dense_by_blocks(U, dims, kap)
+    G5 = _dense_gamma5(v)
+    b = _vec(dims, 98).ravel()
+    mus = [0.2, 0.1, 0.05, 0.02]
+    apply_mu = lambda mu: _ops(U, dims, kap, mu)[0]
+    xs, sts = krylov.serial_shifts(apply_mu, b, mus, tol=1e-12, project=True)
+    assert all(st.converged for st in sts)
+    assert np.array_equal(sts[0].x0, np.zeros_like(b))
+    for i in range(1, len(mus)):
+        Ai = Aw + 1j * mus[i] * G5
+        Q = np.stack(xs[:i]).T                   # n x i
+        d = np.linalg.lstsq(Ai @ Q, b, rcond=None)[0]
+        x0 = Q @ d
+        assert np.linalg.norm(sts[i].x0 - x0) <= 1e-10 * np.linalg.norm(x0), i
+        # and the projected start never has a larger residual than x0 = 0
+        assert np.linalg.norm(b - Ai @ sts[i].x0) <= np.linalg.norm(b)
+        # the solution itself is the dense solve of the shift's system
+        xd = np.linalg.solve(Ai, b)
+        cond = np.linalg.cond(Ai)
+        assert np.linalg.norm(xs[i] - xd) <= 2 * cond * 1e-12 * np.linalg.norm(xd)
+
+
 # ------------------------------------------------------------------ paper's counts
 
 def test_paper_counts_have_cycle_structure():
