@@ -298,19 +298,22 @@ int wd_set_f16_shape(wd_handle h, int nrhs, int R, int threads);
 
 /* The paper has no counterpart to this entry point: it is a service for
  * callers that cannot allocate device memory at the time they apply the
- * operator, e.g. code running while a CUDA graph is being captured (an
- * allocation would break the capture), code that must not synchronise the
- * device (cudaMalloc/cudaFree may), or a process that has handed all device
- * memory to another allocator.  Same result as wd_apply_f32 (FP64 device
- * vectors in and out, FP32 arithmetic inside), but the FP32 links and the
- * two FP32 staging vectors live in one static device array of
- * WD_NOALLOC_SCRATCH_BYTES (64 MiB), held by every GPU that loads the library
- * until the process exits, and the call allocates nothing.
+ * operator, e.g. a process that has handed all device memory to another
+ * allocator (a framework's caching allocator, a fixed budget), or code that
+ * must not synchronise the device (cudaMalloc/cudaFree may).  Same result as
+ * wd_apply_f32 (FP64 device vectors in and out, FP32 arithmetic inside), but
+ * the FP32 links and the two FP32 staging vectors live in one static device
+ * array of WD_NOALLOC_SCRATCH_BYTES (64 MiB), held by every GPU that loads
+ * the library until the process exits, and the call allocates nothing.
  *  - Needs V * (12 + 12 * nrhs) * 16 bytes <= WD_NOALLOC_SCRATCH_BYTES (e.g.
  *    16^4 with nrhs <= 4); larger requests return WD_BAD_ARG.
+ *  - The FP32 links are rebuilt on every call (the array is shared), so at
+ *    small nrhs a call costs more than wd_apply_f32.
  *  - The handle's device must be current.  The first call on each device
- *    looks up the array's device address; make that call before any stream
- *    capture.
+ *    looks up the array's device address and keeps it; make that call before
+ *    any stream capture.  The address is that of the device's primary
+ *    context (the CUDA runtime's): do not call this after resetting the
+ *    device or from another context.
  *  - All calls share the array and keep the last call's contents (every
  *    region is rewritten before it is read); calls whose GPU work overlaps
  *    race, so order them yourself (one stream, or events). */

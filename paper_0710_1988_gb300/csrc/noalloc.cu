@@ -2,23 +2,29 @@
 // that cannot allocate device memory.
 //
 // Some callers cannot call cudaMalloc at the moment they need the operator:
-// code running while a CUDA graph is being captured (an allocation would
-// break the capture), code that must not synchronise the device (cudaMalloc
-// and cudaFree may), and processes that hand all of their device memory to
-// another allocator up front.  wd_apply_f32 needs two FP32 staging vectors
-// and the FP32 copy of the links, which it takes from the handle's pool; this
-// variant keeps all three in one file-scope __device__ array instead, so a
-// call allocates nothing.  The array is WD_NOALLOC_SCRATCH_BYTES (64 MiB) on
-// every GPU that loads the library, held until the process exits.
+// a process that has handed all of its device memory to another allocator
+// up front (a framework's caching allocator, a fixed memory budget), and
+// code that must not synchronise the device (cudaMalloc and cudaFree may).
+// wd_apply_f32 needs two FP32 staging vectors and the FP32 copy of the
+// links, which it takes from the handle's pool; this variant keeps all three
+// in one file-scope __device__ array instead, so a call allocates nothing.
+// The array is WD_NOALLOC_SCRATCH_BYTES (64 MiB) on every GPU that loads the
+// library, held until the process exits.
 //
 // A call needs V * (12 + 12 * nrhs) float4 of it (FP32 links, then the input
 // and output vectors); larger requests are rejected with WD_BAD_ARG.  Every
 // region a call reads is written earlier in the same call, so nothing has to
-// start at zero.  All calls share the array: calls whose GPU work overlaps
+// start at zero.  Because the array is shared, the FP32 links are rebuilt
+// from the handle's FP64 links on every call (about 768 bytes of traffic per
+// site), so at small nrhs a call costs more than wd_apply_f32, which keeps
+// its FP32 links.  All calls share the array: calls whose GPU work overlaps
 // (other streams, other handles, other threads) race and must be ordered by
 // the caller.  The first call on each device looks up the array's device
-// address (cudaGetSymbolAddress, with that device current); make that first
-// call before any stream capture.
+// address (cudaGetSymbolAddress, with that device current) and keeps it for
+// the rest of the process; make that first call before any stream capture.
+// The address belongs to the device's primary context, the one the CUDA
+// runtime uses: a caller that resets the device (cudaDeviceReset) or runs
+// under another context it created must not call this entry point afterwards.
 #include <mutex>
 
 #include "kernels.cuh"

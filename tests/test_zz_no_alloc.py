@@ -1,8 +1,8 @@
 """wd_apply_f32_noalloc: the FP32 operator for callers that cannot allocate
-device memory (inside a graph capture, where the device must not be
-synchronised, or when all device memory belongs to another allocator).  It
-keeps its scratch in a static device array; this file runs last so that a
-failure here stops a run only after every other test has run.
+device memory (a process whose device memory belongs to another allocator,
+or code that must not synchronise the device).  It keeps its scratch in a
+static device array; this file runs last so that a failure here stops a run
+only after every other test has run.
 
 Checked through the C ABI against wd_apply_f32, which allocates its scratch,
 on two calls in a row, within the FP32 operator's tolerance (2e-6 relative)."""
