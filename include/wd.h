@@ -139,6 +139,13 @@ int gmresdr_solve(wd_handle h, const void *b, void *x, int m, int k,
                   double tol, int max_mv, void *V_out, void *Hbar_out,
                   void *theta_out, wd_stats *stats, wd_stream stream);
 
+/* Per-cycle history of the handle's last gmresdr_solve (Sec. 1, Sec. 3): the
+ * least-squares residual norm / ||b - A x0|| at the end of each cycle, the
+ * quantity the convergence test uses.  Copies min(cycles, len) values into
+ * out (host, may be NULL when len = 0) and returns the number of cycles, or
+ * -WD_BAD_ARG for a NULL handle or a negative len. */
+int gmresdr_history(wd_handle h, double *out, int len);
+
 /* Build the deflation space of Sec. 2 once for many right-hand sides:
  * W = A V (k MVPs), G = U^dagger A V and its LU factors.
  *  V: device, k*n complex128, orthonormal columns (e.g. from gmresdr_solve).
@@ -344,6 +351,16 @@ typedef struct {
 int wd_profile_enable(wd_handle h, unsigned mask);
 /* Resolve the recorded events (waits for them) and copy the counters. */
 int wd_profile_read(wd_handle h, wd_profile *out);
+
+/* FP64 fused multiply-add throughput of the current device, measured (not
+ * part of the paper's method: the denominator of the FP64 kernels' roofline,
+ * since every FP64 kernel of the solver path is bound by the FP64 pipe).
+ * Launches 4 blocks of 256 threads per SM, each thread running 8 independent
+ * FMA chains for `iters` steps, `reps` times after one warm-up launch, timed
+ * by CUDA events on `stream` (blocks until done).  *tflops = 2 flops per FMA
+ * / elapsed time; *ms (may be NULL) = time per launch.  1 <= iters <= 2^24,
+ * 1 <= reps <= 1000, else WD_BAD_ARG. */
+int wd_probe_fp64_peak(int iters, int reps, double *tflops, double *ms, wd_stream stream);
 
 /* ---------------------------------------------------------- housekeeping */
 

@@ -21,7 +21,7 @@ import numpy as np
 from . import _lib
 from ._lib import WdError, WdStats, check, lib  # noqa: F401
 
-__all__ = ["WilsonOperator", "Deflation", "WdError", "WdStats", "lib"]
+__all__ = ["WilsonOperator", "Deflation", "WdError", "WdStats", "lib", "probe_fp64_peak"]
 
 
 def _ptr(a) -> int:
@@ -50,6 +50,15 @@ def _stream(stream, *arrays) -> Optional[int]:
             import torch
             return int(torch.cuda.current_stream(a.device).cuda_stream)
     return None
+
+
+def probe_fp64_peak(iters: int = 1 << 15, reps: int = 3, stream=None):
+    """Measured FP64 FMA throughput of the current device: (TFLOP/s, ms per
+    launch) of the library's DFMA probe kernel, timed by CUDA events."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    check(lib().wd_probe_fp64_peak(int(iters), int(reps), ctypes.byref(tf), ctypes.byref(ms),
+                                   _stream(stream)))
+    return tf.value, ms.value
 
 
 class WilsonOperator:
@@ -148,6 +157,16 @@ class WilsonOperator:
             ctypes.byref(st), _stream(stream, b, x))
         check(rc, allow=(_lib.WD_OK, _lib.WD_NOT_CONVERGED))
         return rc, st.as_dict(), hbar[:, :k], theta[:k]
+
+    def gmresdr_history(self):
+        """Least-squares residual / ||r0|| at the end of each cycle of the last
+        gmresdr call on this operator (numpy float64 array)."""
+        c = lib().gmresdr_history(self._h, None, 0)
+        if c < 0:
+            check(-c)
+        out = np.zeros(max(c, 1), dtype=np.float64)
+        lib().gmresdr_history(self._h, out.ctypes.data, c)
+        return out[:c]
 
     def deflation(self, V, k: int, U=None, stream=None) -> "Deflation":
         return Deflation(self, V, k, U, stream)

@@ -69,6 +69,8 @@ SIGNATURES = {
     "wd_eo_reconstruct": (I, [P, P, P, P, I, P]),
     "wd_apply": (I, [P, P, P, I, I, P]),
     "gmresdr_solve": (I, [P, P, P, I, I, D, I, P, P, P, ctypes.POINTER(WdStats), P]),
+    "gmresdr_history": (I, [P, P, I]),
+    "wd_probe_fp64_peak": (I, [I, I, P, P, P]),
     "wd_deflation_create": (I, [P, P, P, I, ctypes.POINTER(P), P]),
     "wd_deflation_destroy": (None, [P]),
     "dbicgstab_solve_deflated": (I, [P, P, P, P, I, D, I, ctypes.POINTER(WdStats), P]),

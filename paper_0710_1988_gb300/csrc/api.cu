@@ -299,6 +299,16 @@ extern "C" int wd_apply(wd_handle h, const void *in, void *out, int nrhs, int da
 
 // ------------------------------------------------------------------ GMRES-DR
 
+extern "C" int gmresdr_history(wd_handle h, double *out, int len) {
+  if (h == nullptr || len < 0 || (len > 0 && out == nullptr)) {
+    set_error("gmresdr_history: NULL handle, negative len or NULL out");
+    return -WD_BAD_ARG;
+  }
+  const int c = (int)h->gmresdr_hist.size();
+  for (int i = 0; i < len && i < c; ++i) out[i] = h->gmresdr_hist[i];
+  return c;
+}
+
 extern "C" int gmresdr_solve(wd_handle h, const void *b, void *x, int m, int k, double tol,
                              int max_mv, void *V_out, void *Hbar_out, void *theta_out,
                              wd_stats *stats, wd_stream stream) {

@@ -202,6 +202,7 @@ int deflate_batched(wd_deflation_space *d, double2 *X, double2 *R0, int nrhs, cu
 int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, double tol,
                 int max_mv, double2 *V_out, double2 *Hbar_host, double2 *theta_host,
                 wd_stats *stats, cudaStream_t s, double *hist_host, int hist_len, Arena &ar) {
+  h->gmresdr_hist.clear();
   const long long n = op_n(h);
   const int nbs = stream_blocks(n), nbw = wilson_blocks(h);
   double2 *Va = ar.take<double2>((size_t)(m + 1) * n);
@@ -381,6 +382,7 @@ int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, doubl
   if (hist_host) {
     for (int i = 0; i < hist_len && i < (int)hist.size(); ++i) hist_host[i] = hist[i];
   }
+  h->gmresdr_hist = hist;
   return rc;
 }
 

@@ -95,6 +95,7 @@ struct wd_context {
   int eo;              // 1: the operator is the even-odd Schur complement on even sites
   double2 *eo_tmp;     // odd half-vector scratch of the Schur operator
   size_t eo_tmp_cap;   // complex numbers
+  std::vector<double> gmresdr_hist;  // last GMRES-DR solve: residual / ||r0|| per cycle
 };
 
 // Length (complex numbers) of the vectors the solvers work on.

@@ -40,3 +40,23 @@ def rel_residual(links, dims, kappa, x, b, mu=0.0):
     x = np.asarray(x).ravel()
     b = np.asarray(b).ravel()
     return np.linalg.norm(b - A(x)) / np.linalg.norm(b)
+
+
+def breakdown_system(dims):
+    """A Wilson system on which BiCGStab breaks down at its first step, exactly.
+
+    Unit links, kappa = 3/16, and b = b1 + b2 with b1 = 1 on (spin 0, colour 0)
+    at every site (momentum 0: A b1 = (1 - 8 kappa) b1 = -b1/2) and b2 =
+    (-1)^x on (spin 0, colours 1, 2) (momentum (pi,0,0,0): A b2 = (1 - 4 kappa)
+    b2 = b2/4).  With x0 = 0 the shadow vector is r_hat = b, and
+    <r_hat, A b> = V (-1/2 + 2/4) = 0 with every term and partial sum a
+    dyadic rational, so the zero is exact in FP64 and FP32 while A b != 0.
+    dims[0] must be even.  Returns (links, kappa, b flat)."""
+    assert dims[0] % 2 == 0
+    v = L.volume(dims)
+    x = np.arange(v) % dims[0]           # site = x + Lx (y + Ly (z + Lz t))
+    b = np.zeros((v, 4, 3), dtype=np.complex128)
+    b[:, 0, 0] = 1.0
+    b[:, 0, 1] = (-1.0) ** x
+    b[:, 0, 2] = (-1.0) ** x
+    return L.unit_gauge_field(dims), 0.1875, b.ravel()

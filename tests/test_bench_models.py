@@ -45,3 +45,31 @@ def test_low_rooflines(eo):
 def test_no_launches_no_lines():
     out = bench.low_rooflines(_prof(0, 0, 0.0, 0, 0.0), 32, 1000, {"hbm_gbs": 1.0}, 0)
     assert out == {}
+
+
+def test_oracle_slices_partition_the_oracle_step():
+    """The CPU baseline and the reference arm time slices that are exactly
+    1/len(sequence) of the oracle's own step: the GMRES-DR Arnoldi sequence
+    (m in the first cycle, m - k in each later one) and the BiCGStab
+    iterations spread evenly over it."""
+    import json
+    import bench
+    from inputs import lattice as L
+    cfg = L.CONFIGS["wilson_16x16x16x16"]
+    with open(bench.ORACLE_COUNTS) as f:
+        counts = json.load(f)
+    js, per = bench.slice_plan(cfg, counts)
+    assert len(js) == cfg.m + (cfg.m - cfg.k) * (counts["gmresdr_cycles"] - 1) == counts["gmresdr_mvp"]
+    assert per * len(js) == sum(counts["dbicgstab_iters"])
+    pos = bench.spread_positions(20, len(js))
+    assert len(set(pos)) == 20 and min(pos) >= 0 and max(pos) < len(js)
+
+
+def test_oracle_slices_run_concurrently():
+    import bench
+    from inputs import lattice as L
+    cfg = L.CONFIGS["wilson_4x4x4x4"]
+    counts = {"gmresdr_cycles": 2, "dbicgstab_iters": [10, 12, 8]}
+    rounds, info = bench.oracle_slices(cfg, 0.12, counts, 2, [0, 3, 20])
+    assert len(rounds) == 3 and all(t > 0 for t in rounds)
+    assert info["js"] == [0, 3, 6] and info["slices_per_step"] == cfg.m + (cfg.m - cfg.k)

@@ -1,0 +1,130 @@
+"""Full-size parity at the benchmark workload (16^4, GMRES-DR(80,40) on one
+Z4 source, then D-BiCGStab(40) on 10 Z4 sources, tol 1e-10, 0.99 kappa_c),
+in the launch configuration bench.py times, against values the oracle alone
+wrote (tests/golden/make_oracle_counts.py, make_solution_projections.py).
+
+Bars, and why:
+  * GMRES-DR (Sec. 1): the same cycle and MVP counts (convergence is tested
+    at cycle ends only, so rounding cannot move the count unless a cycle's
+    residual lands within rounding of tol); the per-cycle least-squares
+    residual within 1e-4 relative (two FP64 Krylov processes of 400 products
+    drift apart by rounding, far less than the cycle-to-cycle decrease);
+    the kept harmonic Ritz values, sorted by |theta|, within 1e-8 relative
+    for the part of the spectrum the restart has converged (residual of the
+    eigenpair small), and as a set within 1e-4 for the rest.
+  * D-BiCGStab (Sec. 2, Sec. 3 counting): every per-source iteration count
+    within 5 % of the oracle's and their sum within 1.5 % (BiCGStab's counts
+    move by a few iterations under rounding: the two runs deflate with bases
+    that agree only to the accuracy of the harmonic Ritz vectors).
+  * Solution error: one source's solution against the oracle's solve to
+    1e-14, through 64 fixed Gaussian probes z_i (Re, Im ~ N(0, 1)):
+    E|<z, e>|^2 = 2 ||e||^2, so the probes estimate the error norm.  At this
+    conditioning a true residual of 1e-10 leaves a relative error of about
+    5e-9 (the oracle's own 1e-10 solve: 4.7e-9, stored with the golden), so
+    the batch solved at 1e-10 must be within twice that, and the same source
+    solved at 1e-11 must meet the 1e-9 bar.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from inputs import lattice as L
+
+from .gpu_util import GOLDEN, cuda, host, kappa_c_table
+
+pytestmark = pytest.mark.gpu
+
+CFG = "wilson_16x16x16x16"
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+@pytest.fixture(scope="module")
+def run():
+    import torch
+
+    import paper_0710_1988_gb300 as wdl
+    cfg = L.CONFIGS[CFG]
+    kappa = cfg.kappa_factor * kappa_c_table()[CFG]["kappa_c"]
+    U = L.gauge_field(cfg.dims, cfg.eps, L.link_seed(cfg))
+    op = wdl.WilsonOperator(cfg.dims, cuda(U), kappa)
+    n = 12 * L.volume(cfg.dims)
+    b0 = cuda(L.source(cfg, 0).ravel())
+    V = torch.zeros(cfg.k * n, dtype=torch.complex128, device="cuda:0")
+    rc, st, hbar, theta = op.gmresdr(b0, torch.zeros_like(b0), cfg.m, cfg.k, cfg.tol, 400000,
+                                     V_out=V)
+    hist = op.gmresdr_history()
+    defl = op.deflation(V, cfg.k)
+    Bh = np.stack([L.source(cfg, j).ravel() for j in range(1, cfg.n_rhs + 1)])
+    X = cuda(np.zeros_like(Bh))
+    rc2, sts = op.dbicgstab(cuda(Bh), X, defl, tol=cfg.tol)
+    X11 = cuda(np.zeros_like(Bh[:1]))
+    rc3, sts11 = op.dbicgstab(cuda(Bh[:1]), X11, defl, tol=1e-11)
+    out = dict(cfg=cfg, kappa=kappa, rc=rc, st=st, theta=theta, hbar=hbar, hist=hist,
+               rc2=rc2, sts=sts, X=host(X), rc3=rc3, X11=host(X11)[0])
+    defl.close()
+    op.close()
+    return out
+
+
+def test_gmresdr_counts_and_history_match_oracle(run):
+    g = _golden(f"oracle_counts_{'x'.join(map(str, run['cfg'].dims))}.json")
+    assert abs(run["kappa"] - g["kappa"]) <= 1e-15
+    assert run["rc"] == 0
+    assert run["st"]["cycles"] == g["gmresdr_cycles"]
+    assert run["st"]["mvp"] == g["gmresdr_mvp"]
+    hist, ho = np.asarray(run["hist"]), np.asarray(g["gmresdr_history"])
+    assert hist.shape == ho.shape
+    assert np.all(np.abs(hist - ho) <= 1e-4 * ho), np.abs(hist / ho - 1).max()
+
+
+def test_harmonic_ritz_values_match_oracle(run):
+    g = _golden(f"oracle_counts_{'x'.join(map(str, run['cfg'].dims))}.json")
+    to = np.array([complex(a, b) for a, b in g["theta"]])
+    tg = np.asarray(run["theta"])
+    assert tg.shape == to.shape
+    # both sides order by (|theta|, Re, Im); compare the sorted moduli and
+    # each value with its nearest counterpart
+    ao, ag = np.sort(np.abs(to)), np.sort(np.abs(tg))
+    rel = np.abs(ag - ao) / ao
+    assert rel.max() <= 1e-4, rel.max()
+    nearest = np.array([np.min(np.abs(to - t)) / abs(t) for t in tg])
+    assert nearest.max() <= 1e-4, nearest.max()
+    # the converged low end of the spectrum agrees to 1e-8
+    assert rel[:10].max() <= 1e-8, rel[:10]
+
+
+def test_dbicgstab_counts_match_oracle(run):
+    g = _golden(f"oracle_counts_{'x'.join(map(str, run['cfg'].dims))}.json")
+    assert run["rc2"] == 0
+    it = np.array([s["iters"] for s in run["sts"]])
+    io = np.array(g["dbicgstab_iters"])
+    assert all(s["converged"] and s["true_rel_res"] <= run["cfg"].tol for s in run["sts"])
+    assert np.all(np.abs(it - io) <= 0.05 * io), (it, io)
+    assert abs(it.sum() - io.sum()) <= 0.015 * io.sum(), (it.sum(), io.sum())
+    assert all(s["mvp"] % 2 == 0 for s in run["sts"])
+
+
+def _probe_error(run, x, p):
+    proj = np.array([complex(a, b) for a, b in p["projections"]])
+    diffs = []
+    for seed, pr in zip(p["probe_seeds"], proj):
+        z = L.gaussian_spinor(run["cfg"].dims, seed).ravel()
+        diffs.append(abs(np.vdot(z, x) - pr))
+    # E|<z, e>|^2 = 2 ||e||^2 for Re, Im ~ N(0, 1) per component
+    return np.sqrt(np.mean(np.square(diffs)) / 2.0) / p["x_norm"]
+
+
+def test_solution_error_against_oracle_solve(run):
+    p = _golden(f"solution_projections_{'x'.join(map(str, run['cfg'].dims))}.json")
+    assert p["rhs"] == 1                    # source 1 is the batch's first system
+    err10 = _probe_error(run, run["X"][0], p)
+    assert err10 <= 2 * p["oracle_tol_1e-10"]["rel_error"], err10
+    assert run["rc3"] == 0
+    err11 = _probe_error(run, run["X11"], p)
+    assert err11 <= 1e-9, err11

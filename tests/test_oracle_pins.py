@@ -588,6 +588,22 @@ def test_serial_shifts_start_from_least_squares_over_previous_solutions():
         assert np.linalg.norm(xs[i] - xd) <= 2 * cond * 1e-12 * np.linalg.norm(xd)
 
 
+def test_bicgstab_reports_breakdown_when_r_hat_is_orthogonal_to_A_r0():
+    """<r_hat, A r0> = 0 exactly (constant + staggered free-field modes at
+    kappa = 3/16, see tests/gpu_util.breakdown_system): alpha is undefined, so
+    BiCGStab stops at its first step with the breakdown flag (the paper's "F"
+    of Sec. 3), having spent one MVP and left x = 0."""
+    from .gpu_util import breakdown_system
+    dims = (4, 2, 2, 2)
+    U, kap, b = breakdown_system(dims)
+    A, _ = _ops(U, dims, kap)
+    assert np.vdot(b, A(b)) == 0 and np.linalg.norm(A(b)) > 0
+    x, st = krylov.bicgstab(A, b, tol=1e-10)
+    assert st.breakdown and not st.converged
+    assert st.iters == 0 and st.mvp == 1
+    assert not np.any(x) and st.true_rel_res == 1.0
+
+
 # ------------------------------------------------------------------ paper's counts
 
 def test_paper_counts_have_cycle_structure():
