@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-growth", action="store_true",
+                    help="skip the growth-row blocks (20^3x32 mixed, 24^3x48 shifts, 32^3x64 "
+                         "forward+backward) of the default line")
     ap.add_argument("--storage", type=int, default=32, choices=[32, 16],
                     help="Krylov vector storage of the mixed workloads")
     ap.add_argument("--mixed-delta", type=float, default=None,
@@ -393,8 +396,10 @@ def gpu_arm(args, cfg, rank, world, local_rank):
         rc, st0, _, _ = op.gmresdr(b0, x0.zero_(), cfg.m, cfg.k, cfg.tol, 400000, V_out=V)
         defl = op.deflation(V, cfg.k)
         res = {}
+        undeflated = lambda B_, X_, d_, tol: op.dbicgstab(B_, X_, None, tol=tol)
         for name, fn, bits in (("fp64", op.dbicgstab, 32), ("mixed", op.dbicgstab_mixed, 32),
-                               ("mixed16", op.dbicgstab_mixed, 16)):
+                               ("mixed16", op.dbicgstab_mixed, 16),
+                               ("fp64_undeflated", undeflated, 32)):
             op.set_mixed_storage(bits)
             X.zero_()
             fn(B, X, defl, tol=cfg.tol)            # warm
@@ -414,7 +419,9 @@ def gpu_arm(args, cfg, rank, world, local_rank):
         defl.close()
         op.set_mixed_storage(32)
         mixed = {
-            "what": "D-BiCGStab(k) on the step's sources with the step's V, projection included",
+            "what": "solves/s as the workload defines it: D-BiCGStab(k) on the step's sources "
+                    "after V and G are set up (the step's V), projection included; FP64 and the "
+                    "mixed forms",
             "fp64_solves_per_s": round(cfg.n_rhs / (res["fp64"][0] * 1e-3), 3),
             "mixed_solves_per_s": round(cfg.n_rhs / (res["mixed"][0] * 1e-3), 3),
             "speedup": round(res["fp64"][0] / res["mixed"][0], 3),
@@ -428,6 +435,13 @@ def gpu_arm(args, cfg, rank, world, local_rank):
             "storage": {"mixed": "FP32 vectors and links", "mixed16": "FP16 p, v, t and links "
                         "(per-site norm), FP32 r, r_hat, x increment"},
             "reliable_every": 50,
+        }
+        mixed["sec2_deflation"] = {
+            "what": "plain BiCGStab (FP64, no projection) on the same sources: the MVPs the "
+                    "projection of Sec. 2 saves on this field",
+            "fp64_undeflated_solves_per_s": round(cfg.n_rhs / (res["fp64_undeflated"][0] * 1e-3), 3),
+            "mvp_deflated": [q["mvp"] for q in res["fp64"][1]],
+            "mvp_undeflated": [q["mvp"] for q in res["fp64_undeflated"][1]],
         }
 
     gst, sts, theta = last
@@ -589,7 +603,7 @@ def main():
         "clocks": res["clocks"],
         "e2e": res["e2e"],
         "counts": res["counts"],
-        "mixed_precision": res["mixed"],
+        "dbicgstab_after_setup": res["mixed"],
         "kernel_breakdown_ms": {k: v for k, v in res["prof_all"].items() if isinstance(v, dict)},
     }
     pa = res["prof_all"]
@@ -607,6 +621,8 @@ def main():
                                     "dbicgstab_alone": eo["dbicgstab_alone"],
                                     "what": "same sources and tolerance, Schur complement on even "
                                             "sites, solutions reconstructed on the full lattice"}
+    if world == 1 and not args.no_growth and cfg.name == "wilson_16x16x16x16":
+        line["growth_rows"] = growth_rows(local_rank, peaks, fp64_peak)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -946,8 +962,7 @@ def grad_arm(args, cfg, rank, world, local_rank):
     mixed_ms = max_over_ranks(sum(ms_mixed), dev)
     op.close()
     peaks = load_json(MEASURED_PEAKS, {}) or {}
-    fp64_peak = {"tflops": round(FP64_FLOPS_PER_CLK_PER_SM * SMS * SM_MAX_MHZ * 1e6 / 1e12, 4),
-                 "source": "derived: 4 FP64 flops/clk/SM x 152 SMs x 2070 MHz"}
+    fp64_peak = measured_fp64_peak(local_rank)
     r = roofline({"prof_live": prof_live}, peaks, fp64_peak)
     r["traffic"] = None
     r.pop("traffic_source", None)
@@ -1059,6 +1074,215 @@ def evenodd_arm(args, cfg, rank, world, local_rank):
 
 
 ROW_ARMS = {"mixed": mixed_arm, "twisted": twisted_arm, "grad": grad_arm, "evenodd": evenodd_arm}
+
+
+# ------------------------------------------------------------------ growth rows in the headline line
+#
+# Short runs of the three growth-row workloads, nested in the default bench
+# line: each block is one warm-up and one timed run (CUDA events on the
+# launching stream, L2 flushed before, clocks sampled), with the roofline of
+# its dominant kernel from one more, profiled run.  `--config <preset>` runs
+# the full row arms above instead.
+
+def _timed_once(fn, flush, stream, local_rank):
+    """One L2-flushed run of fn timed by CUDA events, clocks sampled."""
+    import torch
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    flush.zero_()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1), out, clocks.stop()
+
+
+def growth_mixed(local_rank, peaks):
+    """20^3 x 32 at 0.995 kappa_c, k = 60 (m = 80): GMRES-DR in FP64 gives V
+    (timed as setup), then D-BiCGStab(60) on the 12 Z4 sources in FP64 and in
+    the mixed forms (FP32 and FP16 storage, restarted refinement with FP64
+    true residuals), every solve to 1e-10."""
+    import torch
+    import paper_0710_1988_gb300 as wdl
+    cfg = L.CONFIGS["wilson_20x20x20x32_mixed"]
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    kappa = kappa_for(cfg)
+    U = L.gauge_field(cfg.dims, cfg.eps, L.link_seed(cfg))
+    v = L.volume(cfg.dims)
+    n = 12 * v
+    src = rank_sources(cfg, 0, cfg.n_rhs + 1)
+    b0 = torch.from_numpy(src[0].ravel()).to(dev)
+    B = torch.from_numpy(src[1:].reshape(cfg.n_rhs, n)).to(dev)
+    X = torch.zeros_like(B)
+    V = torch.zeros(cfg.k * n, dtype=torch.complex128, device=dev)
+    op = wdl.WilsonOperator(cfg.dims, torch.from_numpy(U).to(dev), kappa)
+    ms_g, (rc, st, _, _), _ = _timed_once(
+        lambda: op.gmresdr(b0, torch.zeros_like(b0), cfg.m, cfg.k, cfg.tol, 400000, V_out=V),
+        flush, stream, local_rank)
+    if rc != 0:
+        raise RuntimeError(f"20^3x32 GMRES-DR status {rc}")
+    defl = op.deflation(V, cfg.k)
+    out = {}
+    for name, bits in (("fp64", None), ("mixed32", 32), ("mixed16", 16)):
+        if bits:
+            op.set_mixed_storage(bits)
+            op.set_mixed_restart(1e-3, 300)
+
+        def solve():
+            X.zero_()
+            if bits is None:
+                return op.dbicgstab(B, X, defl, tol=cfg.tol)
+            return op.dbicgstab_mixed(B, X, defl, tol=cfg.tol)
+        solve()                                            # warm-up (graphs, autotuner)
+        ms, (rc, ss), clk = _timed_once(solve, flush, stream, local_rank)
+        if rc != 0 or not all(q["converged"] for q in ss):
+            raise RuntimeError(f"20^3x32 {name} D-BiCGStab status {rc}")
+        out[name] = {"solves_per_s": round(cfg.n_rhs / (ms * 1e-3), 3), "ms": round(ms, 1),
+                     "iters": [q["iters"] for q in ss],
+                     "max_true_rel_res": max(q["true_rel_res"] for q in ss), "clocks": clk}
+    # rooflines of the FP32 Wilson kernel and vector updates from one profiled solve
+    op.set_mixed_storage(32)
+    X.zero_()
+    op.profile(mask=0x30)
+    rc, ss = op.dbicgstab_mixed(B, X, defl, tol=cfg.tol)
+    prof = op.profile_read()
+    op.profile(mask=0)
+    roof = low_rooflines(prof, 32, v, peaks, sum(q["iters"] for q in ss))
+    defl.close()
+    op.close()
+    for name in ("mixed32", "mixed16"):
+        out[name]["speedup_vs_fp64"] = round(out[name]["solves_per_s"] / out["fp64"]["solves_per_s"], 3)
+    return {"workload": f"{cfg.name}: D-BiCGStab({cfg.k}) on {cfg.n_rhs} Z4 sources after "
+                        f"GMRES-DR({cfg.m},{cfg.k}) in FP64, tol {cfg.tol:g}, kappa = "
+                        f"{cfg.kappa_factor} kappa_c; mixed = FP32 / FP16 storage, restarted "
+                        f"refinement (delta 1e-3, at most 300 iterations per pass), FP64 true residual",
+            "value": out["mixed32"]["solves_per_s"], "unit": "solves/s",
+            "gmresdr_setup_ms": round(ms_g, 1), "gmresdr_mvp": st["mvp"],
+            "gmresdr_cycles": st["cycles"], "dbicgstab": out,
+            "roofline": roof.get("dslash"), "roofline_updates": roof.get("updates"),
+            "timing": "1 warm-up + 1 timed solve of the batch each"}
+
+
+def growth_twisted(local_rank, peaks, mus=(0.064, 0.032)):
+    """24^3 x 48 twisted mass at kappa_c: the two heaviest shifts, 16 Gaussian
+    sources each, the second projected over the first's solutions (Sec. 4),
+    mixed BiCGStab (FP32, restarted refinement) on the even-odd Schur system,
+    full-lattice solutions to 1e-10."""
+    import torch
+    import paper_0710_1988_gb300 as wdl
+    cfg = L.CONFIGS["twisted_24x24x24x48"]
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    kappa = kappa_for(cfg)
+    U = L.gauge_field(cfg.dims, cfg.eps, L.link_seed(cfg))
+    v = L.volume(cfg.dims)
+    n = 12 * v
+    B = torch.from_numpy(rank_sources(cfg, 0, cfg.n_rhs).reshape(cfg.n_rhs, n)).to(dev)
+    X = torch.zeros(len(mus) * cfg.n_rhs * n, dtype=torch.complex128, device=dev)
+    op = wdl.WilsonOperator(cfg.dims, torch.from_numpy(U).to(dev), kappa)
+    op.set_operator(True)
+    op.set_mixed_storage(32)
+    op.set_mixed_restart(1e-3, 300)
+
+    def run(project=True):
+        X.zero_()
+        rc, sts = op.multishift(B, X, list(mus), tol=cfg.tol, project=project, mixed=True)
+        if rc != 0 or not all(q["converged"] for row in sts for q in row):
+            raise RuntimeError(f"24^3x48 shifts status {rc}")
+        return sts
+    run()
+    ms, sts, clk = _timed_once(run, flush, stream, local_rank)
+    ms_np, sts_np, _ = _timed_once(lambda: run(False), flush, stream, local_rank)
+    op.profile(mask=0x30)
+    sts_p = run()
+    prof = op.profile_read()
+    op.profile(mask=0)
+    roof = low_rooflines(prof, 32, v, peaks, sum(q["iters"] for row in sts_p for q in row), eo=True)
+    op.close()
+    units = cfg.n_rhs * len(mus)
+    return {"workload": f"{cfg.name}: A_W + i mu gamma5 at kappa_c, shifts {list(mus)} heaviest "
+                        f"first, {cfg.n_rhs} Gaussian sources per shift batched, each shift "
+                        f"projected over the earlier solutions (Sec. 4), solved on the even-odd "
+                        f"Schur system by mixed BiCGStab (FP32, restarted refinement delta 1e-3), "
+                        f"full-lattice true residual 1e-10; value counts (source, shift) pairs",
+            "value": round(units / (ms * 1e-3), 3), "unit": "solves/s", "ms": round(ms, 1),
+            "clocks": clk, "unprojected_solves_per_s": round(units / (ms_np * 1e-3), 3),
+            "shifts": [{"mu": mu, "schur_mvp_projected": [q["mvp"] for q in sts[i]],
+                        "schur_mvp_unprojected": [q["mvp"] for q in sts_np[i]],
+                        "max_true_rel_res": max(q["true_rel_res"] for q in sts[i])}
+                       for i, mu in enumerate(mus)],
+            "roofline": roof.get("dslash"), "roofline_updates": roof.get("updates"),
+            "timing": "1 warm-up + 1 timed run each (projected, unprojected)"}
+
+
+def growth_grad(local_rank, fp64_peak):
+    """32^3 x 64 at 0.99 kappa_c: x = A^-1 b and the backward of
+    L = Re(eta^dagger x) (adjoint solve via gamma5, dL/db, dL/dkappa, link
+    force), with both solves in FP64 and in mixed precision, to 1e-10."""
+    import torch
+    import paper_0710_1988_gb300 as wdl
+    from paper_0710_1988_gb300.autograd import wilson_solve
+    cfg = L.CONFIGS["grad_32x32x32x64"]
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    kappa = kappa_for(cfg)
+    U = L.gauge_field(cfg.dims, cfg.eps, L.link_seed(cfg))
+    v = L.volume(cfg.dims)
+    src = rank_sources(cfg, 0, 2)
+    b = torch.from_numpy(src[0].ravel()).to(dev)
+    eta = torch.from_numpy(src[1].ravel()).to(dev)
+    op = wdl.WilsonOperator(cfg.dims, torch.from_numpy(U).to(dev), kappa)
+    op.set_mixed_restart(1e-3, 300)
+
+    def step(mixed):
+        bt = b.clone().requires_grad_(True)
+        kt = torch.tensor(kappa, dtype=torch.float64, requires_grad=True)
+        om = torch.zeros((v, 4, 8), dtype=torch.float64, device=dev, requires_grad=True)
+        x = wilson_solve(bt, kt, om, op, None, cfg.tol, mixed=mixed)
+        loss = (eta.conj() * x).sum().real
+        loss.backward()
+        return float(kt.grad), float(om.grad.abs().max())
+    out = {}
+    for name, mixed in (("fp64", False), ("mixed32", True)):
+        step(mixed)
+        if name == "fp64":
+            op.profile(mask=0x1)
+        ms, res, clk = _timed_once(lambda: step(mixed), flush, stream, local_rank)
+        if name == "fp64":
+            prof_live = op.profile_read()
+            op.profile(mask=0)
+        out[name] = {"value": round(1.0 / (ms * 1e-3), 4), "unit": "fwd+bwd solves/s",
+                     "ms": round(ms, 1), "dkappa": res[0], "max_abs_force": res[1], "clocks": clk}
+    op.close()
+    r = roofline({"prof_live": prof_live}, {}, fp64_peak)
+    r["traffic"] = None
+    r.pop("traffic_source", None)
+    r.pop("hbm_view", None)
+    out["mixed32"]["speedup_vs_fp64"] = round(out["mixed32"]["value"] / out["fp64"]["value"], 3)
+    out["mixed32"]["dkappa_rel_diff_vs_fp64"] = abs(out["mixed32"]["dkappa"] / out["fp64"]["dkappa"] - 1)
+    return {"workload": f"{cfg.name}: x = A^-1 b (BiCGStab) and the backward of Re(eta^dagger x) "
+                        f"(adjoint solve via gamma5, dL/db, dL/dkappa, link force), tol {cfg.tol:g}, "
+                        f"kappa = {cfg.kappa_factor} kappa_c; FP64 and mixed (FP32 iteration, "
+                        f"restarted refinement, FP64 gradients)",
+            "value": out["fp64"]["value"], "unit": "fwd+bwd solves/s", "runs": out,
+            "roofline": r, "timing": "1 warm-up + 1 timed forward+backward each"}
+
+
+def growth_rows(local_rank, peaks, fp64_peak):
+    rows = {}
+    for key, fn in (("wilson_20x20x20x32_mixed", lambda: growth_mixed(local_rank, peaks)),
+                    ("twisted_24x24x24x48", lambda: growth_twisted(local_rank, peaks)),
+                    ("grad_32x32x32x64", lambda: growth_grad(local_rank, fp64_peak))):
+        t = time.perf_counter()
+        rows[key] = fn()
+        rows[key]["wall_s"] = round(time.perf_counter() - t, 1)
+    return rows
 
 
 def reference_arm(args, cfg, rank, world):

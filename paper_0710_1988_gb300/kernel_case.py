@@ -2,6 +2,7 @@
 
     python -m paper_0710_1988_gb300.kernel_case --kernel f32 --lattice 20 20 20 32 --nrhs 12
     python -m paper_0710_1988_gb300.kernel_case --kernel f32 --even-odd --lattice 24 24 24 48 --nrhs 16
+    python -m paper_0710_1988_gb300.kernel_case --kernel fp64-peak --reps 5
 
 Builds a seeded gauge field (U = exp(i 0.5 H)) and Gaussian spinors, then
 applies the operator `--reps` times through the public binding (`apply`,
@@ -24,9 +25,10 @@ def main(argv=None):
     from inputs import lattice as L
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", choices=["f64", "f32", "f16", "mixed"], default="f32",
-                    help="a Wilson apply, or 'mixed': --reps iterations of the FP32 mixed "
-                         "BiCGStab on --nrhs sources (its vector updates and Wilson kernels)")
+    ap.add_argument("--kernel", choices=["f64", "f32", "f16", "mixed", "fp64-peak"], default="f32",
+                    help="a Wilson apply, 'mixed': --reps iterations of the FP32 mixed "
+                         "BiCGStab on --nrhs sources (its vector updates and Wilson kernels), or "
+                         "'fp64-peak': the library's DFMA throughput probe")
     ap.add_argument("--lattice", type=int, nargs=4, default=[20, 20, 20, 32])
     ap.add_argument("--nrhs", type=int, default=12)
     ap.add_argument("--reps", type=int, default=5)
@@ -36,6 +38,12 @@ def main(argv=None):
     ap.add_argument("--even-odd", action="store_true",
                     help="the even-odd Schur operator on even half vectors (f64 and f32 only)")
     args = ap.parse_args(argv)
+    if args.kernel == "fp64-peak":
+        for iters in (1 << 14, 1 << 15, 1 << 16):
+            tf, ms = wdl.probe_fp64_peak(iters=iters, reps=args.reps)
+            print(json.dumps({"kernel": "dfma_probe_kernel", "iters": iters, "reps": args.reps,
+                              "tflops": tf, "ms_per_launch": ms}))
+        return
     dims = tuple(args.lattice)
     U = L.gauge_field(dims, 0.5, 1002)
     psi = L.gaussian_spinor(dims, 2200, nrhs=args.nrhs)
