@@ -289,6 +289,32 @@ int wd_set_mixed_restart(wd_handle h, double delta, int max_inner);
  * Returns WD_BAD_ARG for any other bits. */
 int wd_set_mixed_storage(wd_handle h, int bits);
 
+/* How the wide tall-skinny products V Y (complex128, V of kv <= 88 vectors,
+ * Y kv x ncol with ncol >= 8) are computed: GMRES-DR's restart V_{k+1} =
+ * V_{m+1} P_{k+1} (Sec. 1) and the projection's x0 += V y, r0 -= (A V) y
+ * for batches of right-hand sides (Sec. 2).  tensor_cores = 1 (default):
+ * on the tensor cores by exact-split emulation (each FP64 value as eight
+ * 7-bit BF16 digits against its row's or column's largest exponent, every
+ * partial sum exact in FP32; error of the order of an FP64 product's
+ * rounding relative to row maximum x column maximum, results deterministic);
+ * 0: FP64 fused multiply-adds on the CUDA cores.  Other values: WD_BAD_ARG. */
+int wd_set_contraction(wd_handle h, int tensor_cores);
+
+/* The tall-skinny product itself, without a handle (Sec. 1 restart, Sec. 2
+ * projection updates): for c < ncol,
+ *   OUT[c] = (beta_one ? IN[c] : 0) + sign * sum_{r < kv} V[r] Y[r*ldy + c],
+ * V: kv vectors of n complex128 ([r][n]), Y: kv x ncol complex128 (row
+ * stride ldy >= ncol), IN, OUT: ncol vectors of n; all device pointers.
+ * OUT may alias IN, not V.  tensor_cores = 1: exact-split tensor-core form
+ * (kv <= 88; error of the order of an FP64 product's rounding relative to
+ * row maximum x column maximum), 0: FP64 FMAs (kv <= 128).  Allocates its
+ * small scratch on `stream` (stream-ordered) and waits for the stream.
+ * Returns WD_BAD_ARG (sizes, NULL pointers, host pointers), WD_TIMEOUT
+ * (a wait inside the tensor-core kernel gave up) or WD_CUDA_ERROR. */
+int wd_tsgemm(const void *V, int kv, const void *Y, int ldy, int ncol, const void *IN,
+              void *OUT, int beta_one, double sign, long long n, int tensor_cores,
+              wd_stream stream);
+
 /* out = A in computed by the FP16-storage kernel: in and out are FP64 device
  * vectors in the boundary layout, rounded to the half format on entry
  * (per-site norm, see above) and widened on exit; FP32 arithmetic. */

@@ -21,7 +21,8 @@ import numpy as np
 from . import _lib
 from ._lib import WdError, WdStats, check, lib  # noqa: F401
 
-__all__ = ["WilsonOperator", "Deflation", "WdError", "WdStats", "lib", "probe_fp64_peak"]
+__all__ = ["WilsonOperator", "Deflation", "WdError", "WdStats", "lib", "probe_fp64_peak",
+           "tsgemm"]
 
 
 def _ptr(a) -> int:
@@ -59,6 +60,19 @@ def probe_fp64_peak(iters: int = 1 << 15, reps: int = 3, stream=None):
     check(lib().wd_probe_fp64_peak(int(iters), int(reps), ctypes.byref(tf), ctypes.byref(ms),
                                    _stream(stream)))
     return tf.value, ms.value
+
+
+def tsgemm(V, kv: int, Y, ncol: int, OUT, IN=None, sign: float = 1.0,
+           tensor_cores: bool = True, ldy: Optional[int] = None, stream=None):
+    """OUT[c] = (IN[c] if IN is given else 0) + sign * sum_r V[r] Y[r, c] for
+    complex128 CUDA tensors (V: kv vectors, Y: kv x ncol row-major, OUT and
+    IN: ncol vectors), on the tensor cores or in FP64."""
+    n = _numel(V) // kv
+    check(lib().wd_tsgemm(_ptr(V), int(kv), _ptr(Y), int(ldy or ncol), int(ncol),
+                          _ptr(IN) if IN is not None else None, _ptr(OUT),
+                          1 if IN is not None else 0, float(sign), int(n),
+                          1 if tensor_cores else 0, _stream(stream, V, OUT)))
+    return OUT
 
 
 class WilsonOperator:
@@ -157,6 +171,11 @@ class WilsonOperator:
             ctypes.byref(st), _stream(stream, b, x))
         check(rc, allow=(_lib.WD_OK, _lib.WD_NOT_CONVERGED))
         return rc, st.as_dict(), hbar[:, :k], theta[:k]
+
+    def set_contraction(self, tensor_cores: bool = True):
+        """Wide V*Y products (GMRES-DR restart, projection updates) on the
+        tensor cores (exact-split emulation, default) or in FP64 FMAs."""
+        check(lib().wd_set_contraction(self._h, 1 if tensor_cores else 0))
 
     def gmresdr_history(self):
         """Least-squares residual / ||r0|| at the end of each cycle of the last

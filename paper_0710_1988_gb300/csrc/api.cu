@@ -147,6 +147,7 @@ extern "C" int wd_create(const int lat[4], const void *links, double kappa, doub
   }
   h->eo_tmp = nullptr;
   h->eo_tmp_cap = 0;
+  h->tc_contract = 1;
   for (int i = 0; i < 4; ++i) h->dims[i] = lat[i];
   h->V = V;
   h->n = 12 * V;
@@ -821,6 +822,55 @@ extern "C" int wd_set_mixed_restart(wd_handle h, double delta, int max_inner) {
   if (delta > 0.0 && max_inner < 1) return bad("wd_set_mixed_restart: max_inner must be >= 1");
   h->mixed_delta = delta;
   h->mixed_inner_max = delta > 0.0 ? max_inner : h->mixed_inner_max;
+  return WD_OK;
+}
+
+extern "C" int wd_set_contraction(wd_handle h, int tensor_cores) {
+  if (h == nullptr) return bad("wd_set_contraction: NULL handle");
+  if (tensor_cores != 0 && tensor_cores != 1) return bad("wd_set_contraction: 0 or 1");
+  h->tc_contract = tensor_cores;
+  return WD_OK;
+}
+
+extern "C" int wd_tsgemm(const void *V, int kv, const void *Y, int ldy, int ncol,
+                         const void *IN, void *OUT, int beta_one, double sign, long long n,
+                         int tensor_cores, wd_stream stream) {
+  if (V == nullptr || Y == nullptr || OUT == nullptr || (beta_one && IN == nullptr))
+    return bad("wd_tsgemm: NULL pointer");
+  if (kv < 1 || ncol < 1 || ldy < ncol || n < 1) return bad("wd_tsgemm: bad sizes");
+  if (tensor_cores != 0 && tensor_cores != 1) return bad("wd_tsgemm: tensor_cores must be 0 or 1");
+  if (tensor_cores ? !ts_update_tc_supported(kv, ncol) : kv > 128)
+    return bad("wd_tsgemm: kv must be <= 88 (tensor cores) or <= 128 (FP64)");
+  if (!is_device_pointer(V) || !is_device_pointer(Y) || !is_device_pointer(OUT) ||
+      (beta_one && !is_device_pointer(IN)))
+    return bad("wd_tsgemm: V, Y, IN and OUT must be device memory");
+  cudaStream_t s = (cudaStream_t)stream;
+  const double2 *v = static_cast<const double2 *>(V), *y = static_cast<const double2 *>(Y);
+  const double2 *in = static_cast<const double2 *>(IN);
+  double2 *out = static_cast<double2 *>(OUT);
+  cudaError_t e;
+  if (!tensor_cores) {
+    e = launch_ts_update(v, kv, y, ldy, ncol, in, out, beta_one ? 1 : 0, sign, n, nullptr, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? WD_OK : cuda_fail(e, "wd_tsgemm");
+  }
+  const size_t sb = ts_update_tc_scratch_bytes(kv, ncol);
+  void *scratch = nullptr;
+  e = cudaMallocAsync(&scratch, sb + 256, s);
+  if (e != cudaSuccess) return cuda_fail(e, "wd_tsgemm: scratch");
+  int *err = reinterpret_cast<int *>(static_cast<unsigned char *>(scratch) + sb);
+  int herr = 0;
+  e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e == cudaSuccess)
+    e = launch_ts_update_tc(v, kv, y, ldy, ncol, in, out, beta_one ? 1 : 0, sign, n, scratch, err, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(scratch, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "wd_tsgemm");
+  if (herr != 0) {
+    set_error("wd_tsgemm: a wait in the tensor-core kernel gave up");
+    return WD_TIMEOUT;
+  }
   return WD_OK;
 }
 

@@ -173,16 +173,48 @@ int deflation_build(wd_deflation_space *d, cudaStream_t s, Arena &ar) {
   return WD_OK;
 }
 
+// OUT = (beta_one ? IN : 0) + sign V Y: on the tensor cores (exact-split
+// emulation) when the handle allows it and the product is wide (ncol >= 8),
+// else by FP64 FMAs.  scratch (ts_update_tc_scratch_bytes) and err (device
+// int, set on a tensor-core wait that gave up) may be NULL for the FP64 form.
+static cudaError_t wide_update(const wd_context *h, const double2 *V, int kv, const double2 *Y,
+                               int ldy, int ncol, const double2 *IN, double2 *OUT, int beta_one,
+                               double sign, long long n, void *scratch, int *err, cudaStream_t s) {
+  if (h->tc_contract && scratch != nullptr && err != nullptr && ncol >= 8 &&
+      ts_update_tc_supported(kv, ncol))
+    return launch_ts_update_tc(V, kv, Y, ldy, ncol, IN, OUT, beta_one, sign, n, scratch, err, s);
+  return launch_ts_update(V, kv, Y, ldy, ncol, IN, OUT, beta_one, sign, n, nullptr, s);
+}
+
+static int tc_error_check(int *err, cudaStream_t s) {
+  int herr = 0;
+  WD_CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  WD_CK(cudaStreamSynchronize(s));
+  if (herr != 0) {
+    set_error("tensor-core contraction: a wait in the kernel gave up");
+    return WD_TIMEOUT;
+  }
+  return WD_OK;
+}
+
 int deflate_batched(wd_deflation_space *d, double2 *X, double2 *R0, int nrhs, cudaStream_t s,
                     Arena &ar) {
   const long long n = op_n(d->h);
   const int k = d->k;
   const double2 *Uop = d->U ? d->U : d->V;
   const int g5 = d->U ? 0 : 1;
+  int *tc_err = ar.take<int>(1);
+  if (ar.failed) return WD_OUT_OF_MEMORY;
+  WD_CK(cudaMemsetAsync(tc_err, 0, sizeof(int), s));
+  bool used_tc = false;
   for (int r0 = 0; r0 < nrhs; r0 += 16) {
     const int nc = nrhs - r0 < 16 ? nrhs - r0 : 16;
     double2 *part = ar.take<double2>(ts_dot_partial_count(n, k, nc));
     double2 *C = ar.take<double2>((size_t)k * nc);
+    unsigned char *tcs = d->h->tc_contract && nc >= 8 && ts_update_tc_supported(k, nc)
+                             ? ar.take<unsigned char>(ts_update_tc_scratch_bytes(k, nc))
+                             : nullptr;
+    used_tc |= tcs != nullptr;
     if (ar.failed) return WD_OUT_OF_MEMORY;
     double2 *Xg = X + (size_t)r0 * n, *Rg = R0 + (size_t)r0 * n;
     // c = U^dagger r0 (= V^dagger gamma5 r0 when U = gamma5 V)
@@ -191,10 +223,10 @@ int deflate_batched(wd_deflation_space *d, double2 *X, double2 *R0, int nrhs, cu
     // y = G^{-1} c
     RET_IF(launch_ok(launch_lu_solve(d->LU, d->piv, k, C, nc, s), "lu_solve"));
     // x0 += V y ; r0 -= W y  (W = A V, so r0 = b - A x0 stays exact)
-    RET_IF(launch_ok(launch_ts_update(d->V, k, C, nc, nc, Xg, Xg, 1, 1.0, n, nullptr, s), "ts_update(x)"));
-    RET_IF(launch_ok(launch_ts_update(d->W, k, C, nc, nc, Rg, Rg, 1, -1.0, n, nullptr, s), "ts_update(r)"));
+    RET_IF(launch_ok(wide_update(d->h, d->V, k, C, nc, nc, Xg, Xg, 1, 1.0, n, tcs, tc_err, s), "update(x)"));
+    RET_IF(launch_ok(wide_update(d->h, d->W, k, C, nc, nc, Rg, Rg, 1, -1.0, n, tcs, tc_err, s), "update(r)"));
   }
-  return WD_OK;
+  return used_tc ? tc_error_check(tc_err, s) : WD_OK;
 }
 
 // --------------------------------------------------------------------- GMRES-DR
@@ -232,7 +264,12 @@ int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, doubl
   // WD_TRACE_DENSE=1 prints the SM-clock split of every cycle-end kernel
   const bool trace_dense = std::getenv("WD_TRACE_DENSE") != nullptr;
   long long *clk = trace_dense ? ar.take<long long>(13) : nullptr;
+  const bool tc_restart = h->tc_contract && k + 1 >= 8 && ts_update_tc_supported(m + 1, k + 1);
+  unsigned char *tc_scratch =
+      tc_restart ? ar.take<unsigned char>(ts_update_tc_scratch_bytes(m + 1, k + 1)) : nullptr;
+  int *tc_err = ar.take<int>(1);
   if (ar.failed) return WD_OUT_OF_MEMORY;
+  WD_CK(cudaMemsetAsync(tc_err, 0, sizeof(int), s));
 
   long long mvp = 0, mvp_extra = 0;
   // initial residual (x0 = 0 needs no product)
@@ -328,7 +365,7 @@ int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, doubl
     const bool done = lucky || last_rel <= tol;
     if (!lucky) {
       // V_{k+1} = V_{m+1} P_{k+1} (also after the last cycle, to emit V)
-      RET_IF(launch_ok(launch_ts_update(V, m + 1, P, k + 1, k + 1, nullptr, Vn, 0, 1.0, n, nullptr, s), "restart combine"));
+      RET_IF(launch_ok(wide_update(h, V, m + 1, P, k + 1, k + 1, nullptr, Vn, 0, 1.0, n, tc_scratch, tc_err, s), "restart combine"));
       std::swap(V, Vn);
     }
     if (done) {
@@ -383,6 +420,10 @@ int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, doubl
     for (int i = 0; i < hist_len && i < (int)hist.size(); ++i) hist_host[i] = hist[i];
   }
   h->gmresdr_hist = hist;
+  if (tc_restart && (rc == WD_OK || rc == WD_NOT_CONVERGED)) {
+    const int trc = tc_error_check(tc_err, s);
+    if (trc != WD_OK) return trc;
+  }
   return rc;
 }
 

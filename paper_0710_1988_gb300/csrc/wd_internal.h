@@ -96,6 +96,7 @@ struct wd_context {
   double2 *eo_tmp;     // odd half-vector scratch of the Schur operator
   size_t eo_tmp_cap;   // complex numbers
   std::vector<double> gmresdr_hist;  // last GMRES-DR solve: residual / ||r0|| per cycle
+  int tc_contract;     // 1: wide V*Y products on the tensor cores (exact-split), 0: FP64
 };
 
 // Length (complex numbers) of the vectors the solvers work on.

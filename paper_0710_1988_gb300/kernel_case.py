@@ -3,6 +3,7 @@
     python -m paper_0710_1988_gb300.kernel_case --kernel f32 --lattice 20 20 20 32 --nrhs 12
     python -m paper_0710_1988_gb300.kernel_case --kernel f32 --even-odd --lattice 24 24 24 48 --nrhs 16
     python -m paper_0710_1988_gb300.kernel_case --kernel fp64-peak --reps 5
+    python -m paper_0710_1988_gb300.kernel_case --kernel tsgemm --lattice 16 16 16 16 --kv 81 --ncol 41
 
 Builds a seeded gauge field (U = exp(i 0.5 H)) and Gaussian spinors, then
 applies the operator `--reps` times through the public binding (`apply`,
@@ -25,10 +26,14 @@ def main(argv=None):
     from inputs import lattice as L
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", choices=["f64", "f32", "f16", "mixed", "fp64-peak"], default="f32",
+    ap.add_argument("--kernel", choices=["f64", "f32", "f16", "mixed", "fp64-peak", "tsgemm"],
+                    default="f32",
                     help="a Wilson apply, 'mixed': --reps iterations of the FP32 mixed "
                          "BiCGStab on --nrhs sources (its vector updates and Wilson kernels), or "
-                         "'fp64-peak': the library's DFMA throughput probe")
+                         "'fp64-peak': the library's DFMA throughput probe, 'tsgemm': the "
+                         "restart product V_{m+1} P_{k+1} (--kv, --ncol) in both forms")
+    ap.add_argument("--kv", type=int, default=81)
+    ap.add_argument("--ncol", type=int, default=41)
     ap.add_argument("--lattice", type=int, nargs=4, default=[20, 20, 20, 32])
     ap.add_argument("--nrhs", type=int, default=12)
     ap.add_argument("--reps", type=int, default=5)
@@ -45,6 +50,31 @@ def main(argv=None):
                               "tflops": tf, "ms_per_launch": ms}))
         return
     dims = tuple(args.lattice)
+    if args.kernel == "tsgemm":
+        n = 12 * L.volume(dims)
+        g = torch.Generator(device="cuda").manual_seed(5)
+        V = torch.randn(args.kv * n, dtype=torch.complex128, device="cuda", generator=g)
+        Y = torch.randn(args.kv * args.ncol, dtype=torch.complex128, device="cuda", generator=g)
+        out = {}
+        for tc in (True, False):
+            W = torch.empty(args.ncol * n, dtype=torch.complex128, device="cuda")
+            wdl.tsgemm(V, args.kv, Y, args.ncol, W, tensor_cores=tc)       # warm
+            ts = []
+            for _ in range(args.reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                wdl.tsgemm(V, args.kv, Y, args.ncol, W, tensor_cores=tc)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            out["tensor_cores" if tc else "fp64"] = {"ms": min(ts), "W": W}
+        diff = (out["tensor_cores"]["W"] - out["fp64"]["W"]).abs().max().item()
+        scale = out["fp64"]["W"].abs().max().item()
+        print(json.dumps({"kernel": "tsgemm", "lattice": list(dims), "n": n, "kv": args.kv,
+                          "ncol": args.ncol, "ms_tensor_cores": out["tensor_cores"]["ms"],
+                          "ms_fp64": out["fp64"]["ms"], "max_abs_diff_over_max": diff / scale}))
+        return
     U = L.gauge_field(dims, 0.5, 1002)
     psi = L.gaussian_spinor(dims, 2200, nrhs=args.nrhs)
     op = wdl.WilsonOperator(dims, torch.from_numpy(U).cuda(), args.kappa)
