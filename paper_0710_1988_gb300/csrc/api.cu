@@ -854,7 +854,7 @@ extern "C" int wd_tsgemm(const void *V, int kv, const void *Y, int ldy, int ncol
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return e == cudaSuccess ? WD_OK : cuda_fail(e, "wd_tsgemm");
   }
-  const size_t sb = ts_update_tc_scratch_bytes(kv, ncol);
+  const size_t sb = ts_update_tc_scratch_bytes(kv, ncol, n);
   void *scratch = nullptr;
   e = cudaMallocAsync(&scratch, sb + 256, s);
   if (e != cudaSuccess) return cuda_fail(e, "wd_tsgemm: scratch");

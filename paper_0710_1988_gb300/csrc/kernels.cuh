@@ -119,10 +119,10 @@ cudaError_t launch_ts_update(const double2 *V, int kv, const double2 *Y, int ldy
 
 // The same product on the tensor cores (exact-split BF16 emulation to FP64
 // accuracy, tc_gemm.cu): kv <= 88, any ncol; OUT may alias IN but not V.
-// scratch: ts_update_tc_scratch_bytes(kv, ncol) device bytes; *err (device)
+// scratch: ts_update_tc_scratch_bytes(kv, ncol, n) device bytes; *err (device)
 // is set to 1 if a wait of the kernel gave up (never in normal operation).
 bool ts_update_tc_supported(int kv, int ncol);
-size_t ts_update_tc_scratch_bytes(int kv, int ncol);
+size_t ts_update_tc_scratch_bytes(int kv, int ncol, long long n);
 cudaError_t launch_ts_update_tc(const double2 *V, int kv, const double2 *Y, int ldy, int ncol,
                                 const double2 *IN, double2 *OUT, int beta_one, double sign,
                                 long long n, void *scratch, int *err, cudaStream_t s);

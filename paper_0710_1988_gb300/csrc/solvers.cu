@@ -212,7 +212,7 @@ int deflate_batched(wd_deflation_space *d, double2 *X, double2 *R0, int nrhs, cu
     double2 *part = ar.take<double2>(ts_dot_partial_count(n, k, nc));
     double2 *C = ar.take<double2>((size_t)k * nc);
     unsigned char *tcs = d->h->tc_contract && nc >= 8 && ts_update_tc_supported(k, nc)
-                             ? ar.take<unsigned char>(ts_update_tc_scratch_bytes(k, nc))
+                             ? ar.take<unsigned char>(ts_update_tc_scratch_bytes(k, nc, n))
                              : nullptr;
     used_tc |= tcs != nullptr;
     if (ar.failed) return WD_OUT_OF_MEMORY;
@@ -266,7 +266,7 @@ int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, doubl
   long long *clk = trace_dense ? ar.take<long long>(13) : nullptr;
   const bool tc_restart = h->tc_contract && k + 1 >= 8 && ts_update_tc_supported(m + 1, k + 1);
   unsigned char *tc_scratch =
-      tc_restart ? ar.take<unsigned char>(ts_update_tc_scratch_bytes(m + 1, k + 1)) : nullptr;
+      tc_restart ? ar.take<unsigned char>(ts_update_tc_scratch_bytes(m + 1, k + 1, n)) : nullptr;
   int *tc_err = ar.take<int>(1);
   if (ar.failed) return WD_OUT_OF_MEMORY;
   WD_CK(cudaMemsetAsync(tc_err, 0, sizeof(int), s));
