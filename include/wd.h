@@ -388,6 +388,15 @@ int wd_profile_read(wd_handle h, wd_profile *out);
  * 1 <= reps <= 1000, else WD_BAD_ARG. */
 int wd_probe_fp64_peak(int iters, int reps, double *tflops, double *ms, wd_stream stream);
 
+/* BF16 tensor-core throughput of the current device, measured (not part of
+ * the paper's method: the rate the exact-split contraction of
+ * wd_set_contraction draws on).  One CTA per SM issues `iters` tcgen05 MMAs
+ * of M = 128, N = 256, K = 16 (BF16 in shared memory, FP32 accumulation in
+ * tensor memory), `reps` launches after one warm-up, timed by CUDA events on
+ * `stream`; *tflops counts 2 flops per multiply-add.  1 <= iters <= 2^20,
+ * 1 <= reps <= 100, else WD_BAD_ARG; WD_TIMEOUT if a completion wait gave up. */
+int wd_probe_bf16_mma_peak(int iters, int reps, double *tflops, double *ms, wd_stream stream);
+
 /* ---------------------------------------------------------- housekeeping */
 
 void wd_destroy(wd_handle h);

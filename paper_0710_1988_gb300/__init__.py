@@ -22,7 +22,7 @@ from . import _lib
 from ._lib import WdError, WdStats, check, lib  # noqa: F401
 
 __all__ = ["WilsonOperator", "Deflation", "WdError", "WdStats", "lib", "probe_fp64_peak",
-           "tsgemm"]
+           "tsgemm", "probe_bf16_mma_peak"]
 
 
 def _ptr(a) -> int:
@@ -73,6 +73,15 @@ def tsgemm(V, kv: int, Y, ncol: int, OUT, IN=None, sign: float = 1.0,
                           1 if IN is not None else 0, float(sign), int(n),
                           1 if tensor_cores else 0, _stream(stream, V, OUT)))
     return OUT
+
+
+def probe_bf16_mma_peak(iters: int = 8192, reps: int = 3, stream=None):
+    """Measured BF16 tcgen05 MMA throughput of the current device: (TFLOP/s,
+    ms per launch) of the library's tensor-core probe, timed by CUDA events."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    check(lib().wd_probe_bf16_mma_peak(int(iters), int(reps), ctypes.byref(tf),
+                                       ctypes.byref(ms), _stream(stream)))
+    return tf.value, ms.value
 
 
 class WilsonOperator:

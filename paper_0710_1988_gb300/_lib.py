@@ -71,6 +71,7 @@ SIGNATURES = {
     "gmresdr_solve": (I, [P, P, P, I, I, D, I, P, P, P, ctypes.POINTER(WdStats), P]),
     "gmresdr_history": (I, [P, P, I]),
     "wd_probe_fp64_peak": (I, [I, I, P, P, P]),
+    "wd_probe_bf16_mma_peak": (I, [I, I, P, P, P]),
     "wd_set_contraction": (I, [P, I]),
     "wd_tsgemm": (I, [P, I, P, I, I, P, P, I, D, ctypes.c_longlong, I, P]),
     "wd_deflation_create": (I, [P, P, P, I, ctypes.POINTER(P), P]),

@@ -48,6 +48,10 @@ def main(argv=None):
             tf, ms = wdl.probe_fp64_peak(iters=iters, reps=args.reps)
             print(json.dumps({"kernel": "dfma_probe_kernel", "iters": iters, "reps": args.reps,
                               "tflops": tf, "ms_per_launch": ms}))
+        for iters in (4096, 16384):
+            tf, ms = wdl.probe_bf16_mma_peak(iters=iters, reps=args.reps)
+            print(json.dumps({"kernel": "bf16_mma_probe_kernel", "iters": iters, "reps": args.reps,
+                              "tflops": tf, "ms_per_launch": ms}))
         return
     dims = tuple(args.lattice)
     if args.kernel == "tsgemm":
