@@ -229,6 +229,21 @@ cudaError_t launch_lu_solve(const double2 *LU, const int *piv, int k, double2 *C
 
 // ----------------------------------------------------------------- GMRES-DR cycle end
 
+// Work buffer of the cycle end (complex entries): G (m x k) and T1 ((m+1) x k)
+// in the first 2 (m+1)^2, then the Hessenberg matrix and its transform Z
+// (m x m each, leading dimension m).
+__host__ __device__ inline double2 *cyc_hess(double2 *work, int m, int k) {
+  return work + (size_t)2 * (m + 1) * (m + 1);
+}
+// reflector j of the Hessenberg reduction: u_j (row j of an m x m array,
+// entries j+1 .. iend_j) and (tau_j, iend_j) (tau_j = 0: no reflection)
+__host__ __device__ inline double2 *cyc_zg(double2 *work, int m, int k) {
+  return work + (size_t)2 * (m + 1) * (m + 1) + (size_t)m * m;
+}
+__host__ __device__ inline double2 *cyc_tau(double2 *work, int m, int k) {
+  return work + (size_t)2 * (m + 1) * (m + 1) + (size_t)2 * m * m;
+}
+
 // One thread per line (column of X from the left, row of Y from the right):
 // the left reflection on columns [c0, c1) of X and, in the same pass, the
 // right reflection on rows [0, ny) of Y, both over indices i0..i1.  Each
@@ -382,13 +397,50 @@ __device__ __forceinline__ void givens_lanes(double2 x, double2 y, int ln, doubl
   }
 }
 
-// Schur decomposition of the m x m matrix A (smem, row-major): on return
-// A holds upper triangular T and Z the unitary Schur vectors, A_in = Z T Z^dagger.
+// givens_lanes() for a group of 8 lanes starting at lane `base` (ln = lane -
+// base): four groups of one warp form four independent rotations with the
+// same instructions.  Every lane of the warp calls it (the shuffles take the
+// whole warp); lane 0 of the group writes c and s when `write` is set.
+__device__ __forceinline__ void givens_group(double2 x, double2 y, int ln, int base, bool write,
+                                             double *gc, double2 *gs) {
+  const double f0 = ln == 1 ? y.x : x.x;
+  const double f1 = ln == 0 ? x.x : (ln == 3 ? -y.y : y.x);
+  const double f2 = ln == 1 ? y.y : x.y;
+  const double f3 = ln == 0 ? x.y : (ln == 3 ? y.x : y.y);
+  const double q = fma(f0, f1, f2 * f3);
+  const double a2 = __shfl_sync(0xffffffffu, q, base), b2 = __shfl_sync(0xffffffffu, q, base + 1);
+  const double r = rsqrt(ln == 0 ? a2 : a2 + b2);
+  const double ra = __shfl_sync(0xffffffffu, r, base), rn = __shfl_sync(0xffffffffu, r, base + 1);
+  const double t = ln == 0 ? a2 * ra : ra * rn;
+  const double u = ln == 0 ? t * rn : t * q;
+  const double sx = __shfl_sync(0xffffffffu, u, base + 2), sy = __shfl_sync(0xffffffffu, u, base + 3);
+  if (write && ln == 0) {
+    if (a2 == 0.0) {
+      *gc = 0.0;
+      *gs = make_double2(1.0, 0.0);
+    } else {
+      *gc = u;
+      *gs = make_double2(sx, sy);
+    }
+  }
+}
+
+// Eigenvalues of the m x m matrix A (smem, row-major).  Householder reduction
+// to upper Hessenberg form H = Z^dagger A Z, Z = H_0 H_1 ... the product of
+// the reflectors, which are stored (Ug: u_j as row j; taug: tau_j, last row of
+// u_j) instead of being multiplied out, H is copied to Hg (leading dimension
+// m) for the eigenvector step; then shifted complex QR iteration on the
+// active block only: its
+// diagonal ends up holding the eigenvalues.  Rotations are applied only inside
+// the active window [l, hi]: the parts of T outside it and the Schur vectors
+// never feed back into the iteration, and the eigenvectors come from H by
+// inverse iteration (harmonic_ritz_vector_kernel), so the eigenvalues are those
+// of the full Schur iteration, bit for bit, at a fraction of its FP64 work.
 // Returns 1 if the QR iteration did not converge in 30 m sweeps.
-__device__ int schur_block(double2 *A, double2 *Z, int m, int ld, double2 *u, long long *clk) {
+__device__ int schur_block(double2 *A, int m, int ld, double2 *u, long long *clk, double2 *Hg,
+                           double2 *Ug, double2 *taug) {
   const int tid = threadIdx.x, bd = blockDim.x;
-  for (int e = tid; e < m * m; e += bd)
-    Z[(e / m) * ld + e % m] = (e / m == e % m) ? make_double2(1.0, 0.0) : make_double2(0.0, 0.0);
+  for (int j = tid; j < m; j += bd) taug[j] = make_double2(0.0, 0.0);
   __syncthreads();
   // Householder reduction to upper Hessenberg form.  Each reflector spans
   // rows j+1 .. iend, iend the last nonzero row of column j: after a
@@ -418,8 +470,10 @@ __device__ int schur_block(double2 *A, double2 *Z, int m, int ld, double2 *u, lo
     for (int i = j + 1 + tid; i <= iend; i += bd) u[i] = i == j + 1 ? csub(al, beta) : A[i * ld + j];
     __syncthreads();
     const double tau = 1.0 / (nx * (nx + aa));
-    // H A on columns j..m-1 together with Z H (independent of A), then A H
-    reflect_lines(A, j, m, Z, m, ld, u, tau, j + 1, iend);
+    for (int i = j + 1 + tid; i <= iend; i += bd) Ug[(size_t)j * m + i] = u[i];
+    if (tid == 0) taug[j] = make_double2(tau, (double)iend);
+    // H A on columns j..m-1, then A H
+    reflect_lines(A, j, m, nullptr, 0, ld, u, tau, j + 1, iend);
     __syncthreads();
     reflect_lines(nullptr, 0, 0, A, m, ld, u, tau, j + 1, iend);
     __syncthreads();
@@ -444,20 +498,35 @@ __device__ int schur_block(double2 *A, double2 *Z, int m, int ld, double2 *u, lo
     __syncthreads();
   }
   const double anorm = part > 0.0 ? part : 1.0;
+  for (int e = tid; e < m * m; e += bd) Hg[e] = A[(e / m) * ld + e % m];
+  __syncthreads();
   if (clk != nullptr && tid == 0) clk[7] = clock64();
-  // Shifted QR iteration, one barrier per rotation of a sweep over the
-  // active block [l..hi].  The last warp (rt) computes the shift and every
-  // rotation and applies each rotation to the few entries the next one
-  // depends on; the other warps apply it, in the same barrier interval,
-  // everywhere else: the rest of the active block, the parts of T outside it
-  // and the Schur vectors Z.
-  __shared__ double s_gc[CE_MAXM];
-  __shared__ double2 s_gs[CE_MAXM];
+  // Shifted QR iteration on the active block [l..hi], with up to QR_BULGES
+  // shifts per sweep chased as separate bulges three rows apart.  Warp 4
+  // owns the chains, eight lanes per bulge: at each step a lane group
+  // applies its bulge's current rotation to the entries the next rotation
+  // depends on (rows kk..kk+2 of columns kk, kk+1) and forms the next
+  // rotation, all bulges with the same instructions.  Warps 0-3 apply the
+  // rotations of every active bulge to the rest of the block: the row
+  // rotations in one phase, the column rotations in the next (a row rotation
+  // of one bulge and a column rotation of another can share entries; left
+  // and right rotations commute, so the two phases give the sequential
+  // result).  Bulges three rows apart touch disjoint rows with their row
+  // rotations and disjoint columns with their column rotations within a
+  // step, and an entry meets the rotations of an earlier sweep before those
+  // of a later one, as in one sweep after the other.  (The FP64 unit is
+  // shared by the SM's four schedulers and an FP64 warp instruction holds it
+  // as long with one active lane as with 32: several bulges overlap the
+  // chains of dependent FP64 operations that bound a single sweep.)
+  constexpr int QR_BULGES = 4;            // four lane groups of the chain warp
+  constexpr int QR_CHAIN0 = 4;            // the chain warp (warps 5-7 wait at the barriers)
+  __shared__ double s_gc[3][QR_BULGES];     // rotation of step t in slot t % 3
+  __shared__ double2 s_gs[3][QR_BULGES];
+  __shared__ double2 s_shift[QR_BULGES];
   __shared__ int s_l[2];    // deflation point of the scan, double-buffered
-  const int rt = bd - 32;   // first thread of the rotation warp (the last warp)
-  const int nwk = bd - 32;  // threads of the bulk updates (all warps but the last)
   const int wid = tid >> 5, lane = tid & 31;
-  long long rotations = 0, t_scan = 0, t_rot = 0, t_def = 0, t0 = 0;
+  const int nbulk = 32 * QR_CHAIN0;       // threads of the bulk updates
+  long long rotations = 0, t_scan = 0, t_rot = 0, t0 = 0;
   int hi = m - 1, its = 0, total = 0, scan = 0;
   if (tid < 2) s_l[tid] = 0;
   __syncthreads();
@@ -487,115 +556,149 @@ __device__ int schur_block(double2 *A, double2 *Z, int m, int ld, double2 *u, lo
     }
     ++its;
     ++total;
-    rotations += hi - l;
+    const int w = hi - l + 1;                       // rotations per bulge: w - 1
+    const int nb = w >= 8 ? QR_BULGES : 1;
+    rotations += (long long)nb * (w - 1);
     if (tid == 0) {
       const long long t1 = clock64();
       t_scan += t1 - t0;
       t0 = t1;
-    }
-    if (tid == rt) {
-      const double2 a = A[(hi - 1) * ld + hi - 1], b = A[(hi - 1) * ld + hi];
-      const double2 c = A[hi * ld + hi - 1], d = A[hi * ld + hi];
-      double2 sigma;
-      if (its % 10 == 0) {
-        sigma = cadd(d, make_double2(cabs1(c), 0.0));  // exceptional shift
-      } else {  // eigenvalue of the trailing 2x2 block nearest to d
+      // shifts: the two eigenvalues of the trailing 2 x 2 block (the one
+      // nearest its last diagonal entry first), once per pair of bulges (the
+      // second pair repeats them, as a second double-shift sweep would);
+      // every tenth sweep starts from an exceptional shift
+      {
+        const int r0 = hi - 1;
+        const double2 a = A[(r0) * ld + r0], bb = A[r0 * ld + r0 + 1];
+        const double2 c = A[(r0 + 1) * ld + r0], d = A[(r0 + 1) * ld + r0 + 1];
         const double2 p = cscale(0.5, csub(a, d));
-        const double2 bc = cmul(b, c);
+        const double2 bc = cmul(bb, c);
         double2 q = csqrt_(cadd(cmul(p, p), bc));
         if (p.x * q.x + p.y * q.y < 0.0) q = cneg(q);
         const double2 den = cadd(p, q);
-        sigma = (den.x == 0.0 && den.y == 0.0) ? d : csub(d, cdiv(bc, den));
+        const double2 e1 = (den.x == 0.0 && den.y == 0.0) ? d : csub(d, cdiv(bc, den));
+        const double2 e2 = csub(cadd(a, d), e1);                  // the other eigenvalue
+        for (int b = 0; b < nb; ++b) s_shift[b] = (b & 1) ? e2 : e1;
       }
-      givens(csub(A[l * ld + l], sigma), A[(l + 1) * ld + l], s_gc[l], s_gs[l]);
+      if (its % 10 == 0) s_shift[0] = cadd(A[hi * ld + hi], make_double2(cabs1(A[hi * ld + hi - 1]), 0.0));
     }
-    for (int kk = l; kk < hi; ++kk) {
-      __syncthreads();  // rotation kk published; the updates of rotation kk - 1 done
-      const double gc = s_gc[kk];
-      const double2 gs = s_gs[kk];
-      const double2 mgs = cneg(cconj(gs)), cgs = cconj(gs), ngs = cneg(gs);
-      if (tid >= rt) {
-        // Rotation warp: the entries the next rotation depends on, one per
-        // lane (an FP64 instruction occupies the warp's pipe for the same time
-        // whether 1 or 32 lanes are active, so serial work is spread over
-        // lanes).  Lanes 0..3: row rotation on the 2 x 2 block (kk, kk+1)^2;
-        // then lanes 0..5: column rotation on rows kk..kk+2; then lanes 0..3
-        // form the next rotation from column kk.
-        const int ln = tid - rt;
+    __syncthreads();
+    if (wid == QR_CHAIN0 && lane == 0)
+      givens(csub(A[l * ld + l], s_shift[0]), A[(l + 1) * ld + l], s_gc[0][0], s_gs[0][0]);
+    __syncthreads();
+    const int nsteps = (w - 1) + 3 * (nb - 1);
+    // Step t: the chain warp applies the local part of each bulge's rotation
+    // and forms the rotations of step t+1 while warps 0-3 apply the row
+    // rotations of step t; a barrier of these five warps; then warps 0-3
+    // apply the column rotations of step t (and, after a barrier of their
+    // own, the row rotations of step t+1) while the chain warp goes on with
+    // step t+1.  The chain's entries of step t+1 (rows kk+1..kk+3 of columns
+    // kk+1, kk+2) are written by neither, and a rotation is read from slot
+    // t % 3 while the chain writes slot (t + 2) % 3.  Warps 5-7 wait at the
+    // barrier that ends the sweep.
+    for (int t = 0; t < nsteps; ++t) {
+      const int par = t % 3, nxt = (t + 1) % 3;
+      // ---- phase 1: chains, and the row rotations of every active bulge
+      if (wid == QR_CHAIN0) {
+        const int b = lane >> 3, ln = lane & 7, base = lane & ~7;
+        const int tb = t - 3 * b;
+        const bool act = b < nb && tb >= 0 && tb <= w - 2;
+        const bool enter = b < nb && tb == -1;        // first rotation, for the next step
+        const int kk = act ? l + tb : l;              // a valid index for idle groups
+        const double gc = s_gc[par][b];
+        const double2 gs = s_gs[par][b];
+        const double2 mgs = cneg(cconj(gs)), cgs = cconj(gs), ngs = cneg(gs);
+        // lanes 0..3: row rotation on the 2 x 2 block (kk, kk+1)^2; then
+        // lanes 0..5: column rotation on rows kk..kk+2; then lanes 0..3 form
+        // the next rotation from column kk
         double2 v = make_double2(0.0, 0.0);
-        if (ln < 4) {
+        if (act && ln < 4) {
           const int j = kk + (ln & 1);
-          const double2 t0 = A[kk * ld + j], t1 = A[(kk + 1) * ld + j];
-          v = (ln < 2) ? cadd(cscale(gc, t0), cmul(gs, t1)) : cadd(cmul(mgs, t0), cscale(gc, t1));
-        } else if (ln < 6 && kk + 2 <= hi) {
+          const double2 u0 = A[kk * ld + j], u1 = A[(kk + 1) * ld + j];
+          v = (ln < 2) ? cadd(cscale(gc, u0), cmul(gs, u1)) : cadd(cmul(mgs, u0), cscale(gc, u1));
+        } else if (act && ln < 6 && kk + 2 <= hi) {
           v = A[(kk + 2) * ld + kk + (ln - 4)];
         }
-        const int base = ln & ~1;
+        const int src = base + (ln & 6);
         double2 p0, p1;
-        p0.x = __shfl_sync(0xffffffffu, v.x, base & 31);
-        p0.y = __shfl_sync(0xffffffffu, v.y, base & 31);
-        p1.x = __shfl_sync(0xffffffffu, v.x, (base + 1) & 31);
-        p1.y = __shfl_sync(0xffffffffu, v.y, (base + 1) & 31);
+        p0.x = __shfl_sync(0xffffffffu, v.x, src);
+        p0.y = __shfl_sync(0xffffffffu, v.y, src);
+        p1.x = __shfl_sync(0xffffffffu, v.x, src + 1);
+        p1.y = __shfl_sync(0xffffffffu, v.y, src + 1);
         const double2 o = (ln & 1) == 0 ? cadd(cscale(gc, p0), cmul(cgs, p1))
                                         : cadd(cmul(ngs, p0), cscale(gc, p1));
-        if (ln < 4 || (ln < 6 && kk + 2 <= hi)) A[(kk + (ln >> 1)) * ld + kk + (ln & 1)] = o;
+        if (act && (ln < 4 || (ln < 6 && kk + 2 <= hi))) A[(kk + (ln >> 1)) * ld + kk + (ln & 1)] = o;
         double2 x, y;
-        x.x = __shfl_sync(0xffffffffu, o.x, 2);
-        x.y = __shfl_sync(0xffffffffu, o.y, 2);
-        y.x = __shfl_sync(0xffffffffu, o.x, 4);
-        y.y = __shfl_sync(0xffffffffu, o.y, 4);
-        if (kk + 1 < hi) givens_lanes(x, y, ln, &s_gc[kk + 1], &s_gs[kk + 1]);
-      } else {
-        // Everything else of rotation kk, concurrently, on the other seven
-        // warps; warps 0-2 and 4-6 take the first 192 entries and warp 3
-        // (which shares a scheduler with the rotation warp when warps are
-        // assigned to the four schedulers round-robin) only the overflow:
-        //  - the row rotation on rows kk, kk+1 in the block's columns other
-        //    than kk, kk+1 (c0..kk-1 and kk+2..hi; the bulge entry
-        //    (kk+1, kk-1) becomes 0) and in the columns right of the block;
-        //  - the column rotation on rows l..kk-1, on the rows above the
-        //    block, and on the Schur vectors Z (all m rows).
-        // The rotation warp's entries are disjoint from these, and each
-        // entry outside the block sees the sweep's rotations in order.
-        const int wk = wid == 3 ? 192 + lane : (wid < 3 ? wid : wid - 1) * 32 + lane;
-        const int c0 = kk > l ? kk - 1 : l;
-        const int ncols = hi - c0 - 1;          // block columns, row rotation
-        const int nright = m - 1 - hi;          // columns right of the block
-        const int nrows = kk;                   // rows 0..kk-1 (above and in the block)
-        const int nrot = ncols + nright;
-        for (int t = wk; t < nrot + nrows + m; t += nwk) {
-          if (t < nrot) {
-            const int j = t < ncols ? (c0 + t < kk ? c0 + t : c0 + t + 2) : hi + 1 + (t - ncols);
-            const double2 a1 = A[kk * ld + j], a2 = A[(kk + 1) * ld + j];
-            A[kk * ld + j] = cadd(cscale(gc, a1), cmul(gs, a2));
-            A[(kk + 1) * ld + j] = (kk > l && j == kk - 1) ? make_double2(0.0, 0.0)
-                                                           : cadd(cmul(mgs, a1), cscale(gc, a2));
-          } else {
-            const int q = t - nrot;
-            double2 *X = q < nrows ? A : Z;
-            const int row = q < nrows ? q : q - nrows;
-            const double2 a1 = X[row * ld + kk], a2 = X[row * ld + kk + 1];
-            X[row * ld + kk] = cadd(cscale(gc, a1), cmul(cgs, a2));
-            X[row * ld + kk + 1] = cadd(cmul(ngs, a1), cscale(gc, a2));
-          }
+        x.x = __shfl_sync(0xffffffffu, o.x, base + 2);
+        x.y = __shfl_sync(0xffffffffu, o.y, base + 2);
+        y.x = __shfl_sync(0xffffffffu, o.x, base + 4);
+        y.y = __shfl_sync(0xffffffffu, o.y, base + 4);
+        if (enter) {   // the bulge ahead is three rows on: these entries are settled
+          x = csub(A[l * ld + l], s_shift[b]);
+          y = A[(l + 1) * ld + l];
         }
+        givens_group(x, y, ln, base, (act && kk + 1 < hi) || enter, &s_gc[nxt][b],
+                     &s_gs[nxt][b]);
+      } else if (wid < QR_CHAIN0) {
+        // row rotation of bulge b on rows kk, kk+1, block columns c0..hi
+        // other than kk, kk+1 (the bulge entry (kk+1, kk-1) becomes 0)
+        int off[QR_BULGES + 1];
+        off[0] = 0;
+        for (int b = 0; b < QR_BULGES; ++b) {
+          const int tb = t - 3 * b;
+          const bool act = b < nb && tb >= 0 && tb <= w - 2;
+          const int kk = l + tb;
+          const int c0 = kk > l ? kk - 1 : l;
+          off[b + 1] = off[b] + (act ? hi - c0 - 1 : 0);
+        }
+        for (int e = tid; e < off[QR_BULGES]; e += nbulk) {
+          int b = 0;
+          while (e >= off[b + 1]) ++b;
+          const int kk = l + t - 3 * b;
+          const int c0 = kk > l ? kk - 1 : l;
+          const int u = e - off[b];
+          const int j = c0 + u < kk ? c0 + u : c0 + u + 2;
+          const double gc = s_gc[par][b];
+          const double2 gs = s_gs[par][b], mgs = cneg(cconj(gs));
+          const double2 a1 = A[kk * ld + j], a2 = A[(kk + 1) * ld + j];
+          A[kk * ld + j] = cadd(cscale(gc, a1), cmul(gs, a2));
+          A[(kk + 1) * ld + j] = (kk > l && j == kk - 1) ? make_double2(0.0, 0.0)
+                                                         : cadd(cmul(mgs, a1), cscale(gc, a2));
+        }
+      }
+      if (wid <= QR_CHAIN0) asm volatile("bar.sync 1, %0;" ::"n"(32 * (QR_CHAIN0 + 1)));
+      // ---- phase 2: the column rotations of every active bulge on rows l..kk-1
+      if (wid < QR_CHAIN0) {
+        int off[QR_BULGES + 1];
+        off[0] = 0;
+        for (int b = 0; b < QR_BULGES; ++b) {
+          const int tb = t - 3 * b;
+          const bool act = b < nb && tb >= 0 && tb <= w - 2;
+          off[b + 1] = off[b] + (act ? tb : 0);            // kk - l rows
+        }
+        for (int e = tid; e < off[QR_BULGES]; e += nbulk) {
+          int b = 0;
+          while (e >= off[b + 1]) ++b;
+          const int kk = l + t - 3 * b;
+          const int row = l + (e - off[b]);
+          const double gc = s_gc[par][b];
+          const double2 gs = s_gs[par][b], cgs = cconj(gs), ngs = cneg(gs);
+          const double2 a1 = A[row * ld + kk], a2 = A[row * ld + kk + 1];
+          A[row * ld + kk] = cadd(cscale(gc, a1), cmul(cgs, a2));
+          A[row * ld + kk + 1] = cadd(cmul(ngs, a1), cscale(gc, a2));
+        }
+        asm volatile("bar.sync 2, %0;" ::"n"(32 * QR_CHAIN0));
       }
     }
     __syncthreads();
-    if (tid == 0) {
-      const long long t1 = clock64();
-      t_rot += t1 - t0;
-      t0 = t1;
-    }
-    __syncthreads();
-    if (tid == 0) t_def += clock64() - t0;
+    if (tid == 0) t_rot += clock64() - t0;
   }
   if (clk != nullptr && tid == 0) {
     clk[8] = total;
     clk[9] = rotations;
     clk[10] = t_scan;
     clk[11] = t_rot;
-    clk[12] = t_def;
+    clk[12] = 0;
   }
   return 0;
 }
@@ -605,7 +708,6 @@ __global__ void __launch_bounds__(CE_THREADS) gmresdr_cycle_end_kernel(CycleEndA
   __shared__ int sel[CE_MAXM];
   __shared__ int piv[CE_MAXM];
   const int m = a.m, k = a.k, tid = threadIdx.x, bd = blockDim.x;
-  const int lane = tid & 31, wid = tid >> 5, nw = bd >> 5;
   const int me = *a.m_eff;
   if (tid == 0) {
     a.flags[0] = 0;
@@ -619,7 +721,6 @@ __global__ void __launch_bounds__(CE_THREADS) gmresdr_cycle_end_kernel(CycleEndA
   if (!a.do_restart || me < m) return;
   const double res = a.res[0];
   double2 *P = a.P;
-  const int ldp = k + 1;
   if (k == 0) {  // plain GMRES(m) restart: v_1 = V_{m+1} rho / ||rho||
     for (int i = tid; i <= m; i += bd)
       P[i] = res > 0.0 ? cscale(1.0 / res, a.rho[i]) : make_double2(0.0, 0.0);
@@ -648,7 +749,8 @@ __global__ void __launch_bounds__(CE_THREADS) gmresdr_cycle_end_kernel(CycleEndA
   const double hh = cnorm2(a.H[m * m + m - 1]);
   for (int i = tid; i < m; i += bd) A[i * ld + m - 1] = cadd(A[i * ld + m - 1], cscale(hh, v1[i]));
   __syncthreads();
-  if (schur_block(A, Z, m, ld, v2, a.clk)) {
+  if (schur_block(A, m, ld, v2, a.clk, cyc_hess(a.work, m, k), cyc_zg(a.work, m, k),
+                  cyc_tau(a.work, m, k))) {
     if (tid == 0) a.flags[0] = 1;
     return;
   }
@@ -669,56 +771,159 @@ __global__ void __launch_bounds__(CE_THREADS) gmresdr_cycle_end_kernel(CycleEndA
     if (rank < k) sel[rank] = i;
   }
   __syncthreads();
-  // eigenvectors of T by back substitution, one warp per selected value;
-  // g = Z y written to G (m x k, row-major) in the work buffer
-  double2 *G = a.work;
-  for (int q = wid; q < k; q += nw) {
-    const int i = sel[q];
-    const double2 lam = A[i * ld + i];
-    double2 rhs[3], y[3];  // rows lane, lane+32, lane+64
-#pragma unroll
-    for (int t = 0; t < 3; ++t) {
-      const int row = lane + 32 * t;
-      rhs[t] = row < i ? cneg(A[row * ld + i]) : make_double2(0.0, 0.0);
-      y[t] = row == i ? make_double2(1.0, 0.0) : make_double2(0.0, 0.0);
+  for (int q = tid; q < k; q += bd) a.theta[q] = A[sel[q] * ld + sel[q]];
+#undef STAMP
+}
+
+// Eigenvector of the Hessenberg matrix H (global Hg, leading dimension m)
+// for the selected harmonic Ritz value theta_q, one CTA per q: LU of
+// H - theta I with partial pivoting between the two rows each column
+// touches, two inverse-iteration solves from b = (1, ..., 1), then g = Z y
+// (Z the product of the reduction's stored reflectors), into column q of G
+// (m x k).  theta_q is an eigenvalue of H to rounding, so the solves
+// amplify its eigenvector by the inverse of that rounding; a pivot that is
+// exactly zero is replaced by eps ||H||.
+constexpr int HRV_THREADS = 128;
+
+__global__ void __launch_bounds__(HRV_THREADS) harmonic_ritz_vector_kernel(CycleEndArgs a) {
+  extern __shared__ double2 sm[];
+  const int m = a.m, k = a.k, q = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
+  if (*a.m_eff < m || a.flags[0] != 0) return;        // uniform: no restart basis needed
+  const int ld = cyc_ld(m);
+  double2 *U = sm;                   // m x ld: LU factors of H - theta I
+  double2 *y = U + m * ld;           // m
+  __shared__ double s_mult_re[CE_MAXM], s_mult_im[CE_MAXM];
+  __shared__ int s_swap[CE_MAXM];
+  __shared__ double s_red[HRV_THREADS / 32];
+  const double2 *Hg = cyc_hess(a.work, m, k), *Ug = cyc_zg(a.work, m, k);
+  const double2 theta = a.theta[q];
+  double part = 0.0;
+  for (int e = tid; e < m * m; e += bd) {
+    const int i = e / m, j = e % m;
+    double2 h = Hg[e];
+    part = fmax(part, cabs1(h));
+    if (i == j) h = csub(h, theta);
+    U[i * ld + j] = h;
+  }
+  // ||H|| (largest entry), for the zero-pivot replacement
+  for (int off = 16; off > 0; off >>= 1) part = fmax(part, __shfl_down_sync(0xffffffffu, part, off));
+  if ((tid & 31) == 0) s_red[tid >> 5] = part;
+  __syncthreads();
+  double hn = 0.0;
+  for (int w = 0; w < bd / 32; ++w) hn = fmax(hn, s_red[w]);
+  const double tiny = 2.220446049250313e-16 * (hn > 0.0 ? hn : 1.0);
+  // LU of the Hessenberg matrix: column j has nonzeros in rows <= j + 1
+  for (int j = 0; j + 1 < m; ++j) {
+    const double2 p0 = U[j * ld + j], p1 = U[(j + 1) * ld + j];
+    const bool sw = cabs1(p1) > cabs1(p0);
+    __syncthreads();
+    if (sw)
+      for (int c = j + tid; c < m; c += bd) {
+        const double2 t0 = U[j * ld + c];
+        U[j * ld + c] = U[(j + 1) * ld + c];
+        U[(j + 1) * ld + c] = t0;
+      }
+    __syncthreads();
+    double2 piv = U[j * ld + j];
+    if (piv.x == 0.0 && piv.y == 0.0) piv = make_double2(tiny, 0.0);
+    const double2 l = cdiv(U[(j + 1) * ld + j], piv);
+    if (tid == 0) {
+      s_swap[j] = sw ? 1 : 0;
+      s_mult_re[j] = l.x;
+      s_mult_im[j] = l.y;
+      U[j * ld + j] = piv;
     }
-    const double smin = fmax(2.220446049250313e-16 * (cabs1(lam) + 1e-300), 1e-290);
-    for (int j = i - 1; j >= 0; --j) {
-      const int own = j & 31, slot = j >> 5;
-      double2 yj = make_double2(0.0, 0.0);
-      if (lane == own) {
-        double2 den = csub(A[j * ld + j], lam);
-        if (cabs1(den) < smin) den = make_double2(smin, 0.0);
-        const double2 r = slot == 0 ? rhs[0] : (slot == 1 ? rhs[1] : rhs[2]);
-        yj = cdiv(r, den);
-        if (slot == 0) y[0] = yj;
-        else if (slot == 1) y[1] = yj;
-        else y[2] = yj;
-      }
-      yj.x = __shfl_sync(0xffffffffu, yj.x, own);
-      yj.y = __shfl_sync(0xffffffffu, yj.y, own);
-#pragma unroll
-      for (int t = 0; t < 3; ++t) {
-        const int row = lane + 32 * t;
-        if (row < j) rhs[t] = csub(rhs[t], cmul(A[row * ld + j], yj));
+    for (int c = j + 1 + tid; c < m; c += bd)
+      U[(j + 1) * ld + c] = csub(U[(j + 1) * ld + c], cmul(l, U[j * ld + c]));
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const double2 pl = U[(m - 1) * ld + m - 1];
+    if (pl.x == 0.0 && pl.y == 0.0) U[(m - 1) * ld + m - 1] = make_double2(tiny, 0.0);
+  }
+  for (int i = tid; i < m; i += bd) y[i] = make_double2(1.0, 0.0);
+  __syncthreads();
+  for (int it = 0; it < 2; ++it) {
+    // forward: apply the row swaps and multipliers (one thread, a short chain)
+    if (tid == 0) {
+      for (int j = 0; j + 1 < m; ++j) {
+        if (s_swap[j]) {
+          const double2 t0 = y[j];
+          y[j] = y[j + 1];
+          y[j + 1] = t0;
+        }
+        y[j + 1] = csub(y[j + 1], cmul(make_double2(s_mult_re[j], s_mult_im[j]), y[j]));
       }
     }
-    // g = Z y
-#pragma unroll
-    for (int t = 0; t < 3; ++t) {
-      const int row = lane + 32 * t;
-      double2 g = make_double2(0.0, 0.0);
-      for (int j = 0; j <= i; ++j) {
-        const int own = j & 31, slot = j >> 5;
-        double2 yj = slot == 0 ? y[0] : (slot == 1 ? y[1] : y[2]);
-        yj.x = __shfl_sync(0xffffffffu, yj.x, own);
-        yj.y = __shfl_sync(0xffffffffu, yj.y, own);
-        if (row < m) g = cfma(Z[row * ld + j], yj, g);
-      }
-      if (row < m) G[row * k + q] = g;
+    __syncthreads();
+    // back substitution, column oriented: y_j = y_j / u_jj, then y_i -= u_ij y_j
+    for (int j = m - 1; j >= 0; --j) {
+      const double2 yj = cdiv(y[j], U[j * ld + j]);
+      __syncthreads();
+      if (tid == 0) y[j] = yj;
+      for (int i = tid; i < j; i += bd) y[i] = csub(y[i], cmul(U[i * ld + j], yj));
+      __syncthreads();
+    }
+    // normalise (the first solve's vector can be very large)
+    double n2 = 0.0, mx = 0.0;
+    for (int i = tid; i < m; i += bd) mx = fmax(mx, cabs1(y[i]));
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
+    if ((tid & 31) == 0) s_red[tid >> 5] = mx;
+    __syncthreads();
+    mx = 0.0;
+    for (int w = 0; w < bd / 32; ++w) mx = fmax(mx, s_red[w]);
+    __syncthreads();
+    const double inv = mx > 0.0 ? 1.0 / mx : 1.0;
+    for (int i = tid; i < m; i += bd) {
+      y[i] = cscale(inv, y[i]);
+      n2 += cnorm2(y[i]);
+    }
+    for (int off = 16; off > 0; off >>= 1) n2 += __shfl_down_sync(0xffffffffu, n2, off);
+    if ((tid & 31) == 0) s_red[tid >> 5] = n2;
+    __syncthreads();
+    n2 = 0.0;
+    for (int w = 0; w < bd / 32; ++w) n2 += s_red[w];
+    __syncthreads();
+    const double inv2 = n2 > 0.0 ? 1.0 / sqrt(n2) : 1.0;
+    for (int i = tid; i < m; i += bd) y[i] = cscale(inv2, y[i]);
+    __syncthreads();
+  }
+  // g = Z y = H_0 (H_1 (... (H_{m-3} y))) by the stored reflectors, one
+  // warp, then into column q of G
+  if (tid < 32) {
+    const double2 *taug = cyc_tau(a.work, m, k);
+    for (int j = m - 3; j >= 0; --j) {
+      const double2 ti = taug[j];
+      if (ti.x == 0.0) continue;                       // uniform: no reflection
+      const int iend = (int)ti.y;
+      double2 sdot = make_double2(0.0, 0.0);
+      for (int i = j + 1 + tid; i <= iend; i += 32) sdot = cfmac(Ug[(size_t)j * m + i], y[i], sdot);
+      sdot = warp_csum_all(sdot);
+      const double2 f = cscale(ti.x, sdot);
+      for (int i = j + 1 + tid; i <= iend; i += 32)
+        y[i] = csub(y[i], cmul(Ug[(size_t)j * m + i], f));
+      __syncwarp();
     }
   }
   __syncthreads();
+  double2 *G = a.work;
+  for (int i = tid; i < m; i += bd) G[i * k + q] = y[i];
+}
+
+// The restarted basis from the harmonic Ritz vectors G (m x k, columns):
+// P_k = QR of [G; 0], p_{k+1} = rho orthonormalised, Hbar_k, c_k.
+__global__ void __launch_bounds__(CE_THREADS) gmresdr_restart_basis_kernel(CycleEndArgs a) {
+  extern __shared__ double2 sm[];
+  const int m = a.m, k = a.k, tid = threadIdx.x, bd = blockDim.x;
+  const int lane = tid & 31, wid = tid >> 5, nw = bd >> 5;
+  if (*a.m_eff < m || a.flags[0] != 0) return;        // uniform
+  double2 *P = a.P;
+  const int ldp = k + 1;
+  double2 *v1 = sm;                  // m+1
+  double2 *v2 = v1 + (m + 1);        // m+1
+  double2 *G = a.work;
+#define STAMP(i) \
+  if (a.clk != nullptr && tid == 0) a.clk[i] = clock64();
   STAMP(4)
   // P_k = QR of [g_1..g_k; 0] by Gram-Schmidt applied twice; p_{k+1} from rho
   double2 *coef = v2;
@@ -769,11 +974,11 @@ __global__ void __launch_bounds__(CE_THREADS) gmresdr_cycle_end_kernel(CycleEndA
     for (int i = 0; i <= m; ++i) s = cfmac(P[i * ldp + r], a.rho[i], s);
     a.ck[r] = s;
   }
-  for (int q = tid; q < k; q += bd) a.theta[q] = A[sel[q] * ld + sel[q]];
   __syncthreads();
   STAMP(6)
 #undef STAMP
 }
+
 
 size_t gmresdr_cycle_end_smem(int m) {
   const size_t lsq = (size_t)(m + 1) * cyc_ld(m) + 3 * (m + 1);
@@ -785,11 +990,31 @@ cudaError_t launch_gmresdr_cycle_end(const CycleEndArgs &a, cudaStream_t s) {
   ProfLaunch prof_(PC_DENSE, s);
   if (a.m > CE_MAXM || a.m < 1 || a.k < 0 || a.k >= a.m) return cudaErrorInvalidValue;
   const size_t smem = gmresdr_cycle_end_smem(a.m);
-  cudaError_t e = cudaFuncSetAttribute(gmresdr_cycle_end_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)gmresdr_cycle_end_smem(CE_MAXM));
+  const size_t smem_vec = ((size_t)a.m * cyc_ld(a.m) + a.m) * sizeof(double2);
+  static thread_local int attr_device = -1;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  if (attr_device != dev) {
+    e = cudaFuncSetAttribute(gmresdr_cycle_end_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)gmresdr_cycle_end_smem(CE_MAXM));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(harmonic_ritz_vector_kernel,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(((size_t)CE_MAXM * cyc_ld(CE_MAXM) + CE_MAXM) * sizeof(double2)));
+    if (e != cudaSuccess) return e;
+    attr_device = dev;
+  }
   gmresdr_cycle_end_kernel<<<1, CE_THREADS, smem, s>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || !a.do_restart || a.k == 0) return e;
+  // harmonic Ritz vectors by inverse iteration, one CTA per kept value, then
+  // the restarted basis (both return at once after a lucky breakdown or a
+  // failed eigenvalue iteration)
+  harmonic_ritz_vector_kernel<<<a.k, HRV_THREADS, smem_vec, s>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  gmresdr_restart_basis_kernel<<<1, CE_THREADS, 2 * (a.m + 1) * sizeof(double2), s>>>(a);
   return cudaGetLastError();
 }
 

@@ -163,7 +163,7 @@ struct CycleEndArgs {
   double2 *ck;         // k+1: P^dagger rho
   double2 *theta;      // k harmonic Ritz values
   int *flags;          // [0] eig failure, [1] lucky
-  double2 *work;       // scratch >= 2*(m+1)*(m+1) complex
+  double2 *work;       // scratch >= 2*(m+1)*(m+1) + 2*m*m + m complex
   long long *clk;      // nullptr, or 10 slots: SM clock at phase boundaries, QR sweeps, rotations
   int do_restart;
 };

@@ -260,7 +260,7 @@ int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, doubl
   int *flags = ar.take<int>(2);
   int *status = ar.take<int>(1);
   int *m_eff = ar.take<int>(1);
-  double2 *work = ar.take<double2>((size_t)2 * (m + 1) * (m + 1));
+  double2 *work = ar.take<double2>((size_t)2 * (m + 1) * (m + 1) + (size_t)2 * m * m + m);
   // WD_TRACE_DENSE=1 prints the SM-clock split of every cycle-end kernel
   const bool trace_dense = std::getenv("WD_TRACE_DENSE") != nullptr;
   long long *clk = trace_dense ? ar.take<long long>(13) : nullptr;
