@@ -65,3 +65,28 @@ def test_stats_struct_layout():
     from paper_0710_1988_gb300._lib import WdStats
     # long long x2, int x5, (pad), double x3
     assert ctypes.sizeof(WdStats) == 8 * 2 + 4 * 5 + 4 + 8 * 3
+
+
+def test_new_entry_points_reject_bad_arguments_without_a_gpu(lib):
+    """The contraction, history, probe and setter entry points check their
+    arguments before touching the device."""
+    from paper_0710_1988_gb300 import _lib
+    # wd_tsgemm: NULL pointers, bad sizes, bad mode, kv beyond the tensor-core limit
+    assert lib.wd_tsgemm(None, 4, None, 8, 8, None, None, 0, 1.0, 100, 1, None) == _lib.WD_BAD_ARG
+    p = ctypes.c_void_p(16)
+    assert lib.wd_tsgemm(p, 0, p, 8, 8, None, p, 0, 1.0, 100, 1, None) == _lib.WD_BAD_ARG
+    assert lib.wd_tsgemm(p, 4, p, 4, 8, None, p, 0, 1.0, 100, 1, None) == _lib.WD_BAD_ARG  # ldy < ncol
+    assert lib.wd_tsgemm(p, 4, p, 8, 8, None, p, 0, 1.0, 100, 2, None) == _lib.WD_BAD_ARG
+    assert lib.wd_tsgemm(p, 89, p, 8, 8, None, p, 0, 1.0, 100, 1, None) == _lib.WD_BAD_ARG
+    assert "88" in _lib.last_error()
+    assert lib.wd_tsgemm(p, 129, p, 8, 8, None, p, 0, 1.0, 100, 0, None) == _lib.WD_BAD_ARG
+    assert lib.wd_tsgemm(p, 4, p, 8, 8, None, p, 1, 1.0, 100, 1, None) == _lib.WD_BAD_ARG  # IN NULL
+    # gmresdr_history: NULL handle or negative length
+    assert lib.gmresdr_history(None, None, 0) == -_lib.WD_BAD_ARG
+    # wd_set_contraction: NULL handle
+    assert lib.wd_set_contraction(None, 1) == _lib.WD_BAD_ARG
+    # probes: bad sizes
+    out = ctypes.c_double()
+    assert lib.wd_probe_fp64_peak(0, 1, ctypes.byref(out), None, None) == _lib.WD_BAD_ARG
+    assert lib.wd_probe_bf16_mma_peak(1, 0, ctypes.byref(out), None, None) == _lib.WD_BAD_ARG
+    assert lib.wd_probe_bf16_mma_peak(1, 1, None, None, None) == _lib.WD_BAD_ARG
