@@ -552,6 +552,103 @@ cudaError_t launch_ts_update(const double2 *V, int kv, const double2 *Y, int ldy
   return cudaSuccess;
 }
 
+// ----------------------------------------------------------------- CGS correction
+
+// w -= V h for the second pass of classical Gram-Schmidt, whose coefficients
+// h are of the order of the first pass's rounding (|h| ~ eps ||w||): the
+// correction V h then needs only FP32 accuracy relative to itself, which is
+// far below FP64 rounding of w, while its products would cost FP64 FMAs.
+// FP32 path, taken when ||h||^2 <= 1e-20 (||w0||^2 - ||hsum||^2) (the
+// correction below 1e-10 of the vector it corrects; ||w0||^2 from the Wilson
+// kernel's partials, hsum the coefficients of both passes): V and h are
+// truncated to FP32 by bit operations (no FP64 instruction), the products
+// accumulate in FP32, and w is updated in FP64.  Otherwise the FP64 form of
+// ts_update.  Every block forms the decision from the same device data in
+// the same order, so all take the same path.
+__device__ __forceinline__ float f32_trunc(double x) {
+  const long long b = __double_as_longlong(x);
+  const unsigned sign = (unsigned)((unsigned long long)b >> 32) & 0x80000000u;
+  const int fe = (int)((b >> 52) & 0x7FF) - 1023 + 127;
+  if (fe <= 0) return __uint_as_float(sign);                 // below FP32's normal range
+  if (fe >= 255) return __uint_as_float(sign | 0x7F7FFFFFu);  // clamp (not met here)
+  return __uint_as_float(sign | ((unsigned)fe << 23) | ((unsigned)(b >> 29) & 0x7FFFFFu));
+}
+
+__device__ __forceinline__ double f64_widen(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned e = (u >> 23) & 0xFF;
+  if (e == 0) return __longlong_as_double((long long)sign);  // zero (subnormals flushed)
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(e - 127 + 1023) << 52) |
+                                          ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+
+__global__ void __launch_bounds__(TU_THREADS)
+ts_update_correction_kernel(const double2 *__restrict__ V, int kv, const double2 *__restrict__ h,
+                            const double2 *__restrict__ hsum, int ldh,
+                            const double *__restrict__ part_w, int nbw, double2 *w, long long n,
+                            const int *__restrict__ status) {
+  if (status != nullptr && *status != 0) return;
+  __shared__ float2 hf[TU_MAXK];
+  __shared__ double2 hd[TU_MAXK];
+  __shared__ int use32;
+  if (threadIdx.x < 32) {
+    double w2 = 0.0, s2 = 0.0, c2 = 0.0;
+    for (int b = threadIdx.x; b < nbw; b += 32) w2 += part_w[(long long)b * 3 + 2];
+    for (int r = threadIdx.x; r < kv; r += 32) {
+      c2 += cnorm2(h[r]);
+      s2 += cnorm2(hsum[(long long)r * ldh]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      w2 += __shfl_xor_sync(0xffffffffu, w2, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+    }
+    if (threadIdx.x == 0) use32 = c2 <= 1e-20 * (w2 - s2) ? 1 : 0;
+  }
+  for (int r = threadIdx.x; r < kv; r += blockDim.x) {
+    hd[r] = h[r];
+    hf[r] = make_float2(f32_trunc(h[r].x), f32_trunc(h[r].y));
+  }
+  __syncthreads();
+  const bool fp32 = use32 != 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double2 o = w[i];
+    if (fp32) {
+      float ax = 0.f, ay = 0.f;
+      for (int r = 0; r < kv; ++r) {
+        const double2 v = __ldg(V + (long long)r * n + i);
+        const float vx = f32_trunc(v.x), vy = f32_trunc(v.y);
+        const float2 c = hf[r];
+        ax = fmaf(vx, c.x, fmaf(-vy, c.y, ax));
+        ay = fmaf(vx, c.y, fmaf(vy, c.x, ay));
+      }
+      o.x -= f64_widen(ax);
+      o.y -= f64_widen(ay);
+    } else {
+      double2 acc = make_double2(0.0, 0.0);
+      for (int r = 0; r < kv; ++r) acc = cfma(__ldg(V + (long long)r * n + i), hd[r], acc);
+      o = csub(o, acc);
+    }
+    w[i] = o;
+  }
+}
+
+cudaError_t launch_ts_update_correction(const double2 *V, int kv, const double2 *h,
+                                        const double2 *hsum, int ldh, const double *part_w,
+                                        int nbw, double2 *w, long long n, const int *status,
+                                        cudaStream_t s) {
+  ProfLaunch prof_(PC_TS, s);
+  if (kv > TU_MAXK || kv < 1) return cudaErrorInvalidValue;
+  long long blocks = (n + TU_THREADS - 1) / TU_THREADS;
+  if (blocks > 1216) blocks = 1216;
+  ts_update_correction_kernel<<<(unsigned)blocks, TU_THREADS, 0, s>>>(V, kv, h, hsum, ldh, part_w,
+                                                                     nbw, w, n, status);
+  return cudaGetLastError();
+}
+
 // ----------------------------------------------------------------- Arnoldi helpers
 
 __global__ void arnoldi_normalize_finalize_kernel(const double *__restrict__ pw, int nb,

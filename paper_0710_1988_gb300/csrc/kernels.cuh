@@ -117,6 +117,14 @@ cudaError_t launch_ts_update(const double2 *V, int kv, const double2 *Y, int ldy
                              const double2 *IN, double2 *OUT, int beta_one, double sign,
                              long long n, const int *status, cudaStream_t s);
 
+// w -= V h for the second classical Gram-Schmidt pass: FP32 products when
+// ||h||^2 <= 1e-20 (||w0||^2 - ||hsum||^2) (part_w: Wilson-kernel partials,
+// [3 b + 2] = block b's share of ||w0||^2; hsum: column of both passes'
+// coefficients, stride ldh), else FP64 (blas.cu).
+cudaError_t launch_ts_update_correction(const double2 *V, int kv, const double2 *h,
+                                        const double2 *hsum, int ldh, const double *part_w,
+                                        int nbw, double2 *w, long long n, const int *status,
+                                        cudaStream_t s);
 // The same product on the tensor cores (exact-split BF16 emulation to FP64
 // accuracy, tc_gemm.cu): kv <= 88, any ncol; OUT may alias IN but not V.
 // scratch: ts_update_tc_scratch_bytes(kv, ncol, n) device bytes; *err (device)

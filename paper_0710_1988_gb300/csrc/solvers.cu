@@ -320,7 +320,7 @@ int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, doubl
       RET_IF(launch_ok(launch_ts_update(V, j + 1, H + j, m, 1, w, w, 1, -1.0, n, status, s), "cgs upd1"));
       RET_IF(launch_ok(launch_ts_dot(V, j + 1, w, 1, 0, n, part_t, status, s), "cgs dot2"));
       RET_IF(launch_ok(launch_ts_dot_finalize(part_t, n, j + 1, 1, h2, 1, H + j, m, status, s), "cgs fin2"));
-      RET_IF(launch_ok(launch_ts_update(V, j + 1, h2, 1, 1, w, w, 1, -1.0, n, status, s), "cgs upd2"));
+      RET_IF(launch_ok(launch_ts_update_correction(V, j + 1, h2, H + j, m, part_w, nbw, w, n, status, s), "cgs upd2"));
       // h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}
       RET_IF(launch_ok(launch_norms(w, nullptr, part_n, n, 1, s), "norm w"));
       RET_IF(launch_ok(launch_arnoldi_normalize_finalize(part_n, nbs, part_w, nbw, H, m, j, 1e-14, status, m_eff, s), "arnoldi fin"));
