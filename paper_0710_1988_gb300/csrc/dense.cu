@@ -3,15 +3,18 @@
 //  * LU with partial pivoting and triangular solves: the k x k projected
 //    system (U^dagger A V) y = U^dagger r0 of Sec. 2.
 //  * The end of a GMRES-DR(m,k) cycle (Morgan's deflated restarting, cited
-//    in Sec. 1): least squares min ||c - Hbar d|| by Householder QR, the
-//    harmonic Ritz pairs of H_m + |h_{m+1,m}|^2 f e_m^T (f = H_m^{-dagger}
-//    e_m) by Householder reduction to Hessenberg form and complex shifted
-//    QR iteration (Schur form, then eigenvectors by back substitution),
-//    selection of the k smallest |theta|, the orthonormal P_{k+1}, and the
-//    restarted Hbar_k = P_{k+1}^dagger Hbar_m P_k, c = P_{k+1}^dagger rho.
+//    in Sec. 1): least squares min ||c - Hbar d|| by Householder QR; the
+//    harmonic Ritz matrix M = H_m + |h_{m+1,m}|^2 f e_m^T (f = H_m^{-dagger}
+//    e_m, by a banded LU of H_m); every eigenvalue of M estimated in FP32
+//    (Householder reduction to Hessenberg form, shifted QR iteration), each
+//    estimate refined in FP64 by inverse iteration on M (one CTA each), the
+//    refined pairs checked and the k smallest |theta| kept (if the check
+//    fails: FP64 reduction and QR iteration, eigenvectors by inverse
+//    iteration on the Hessenberg form); then the orthonormal P_{k+1}, the
+//    restarted Hbar_k = P_{k+1}^dagger Hbar_m P_k and c = P_{k+1}^dagger rho.
 //
-// Matrices are small (m <= 80, k <= 128); these kernels run one CTA and
-// keep their working matrices in shared memory.  Every loop is bounded.
+// Matrices are small (m <= 80, k <= 128); these kernels keep their working
+// matrices in shared memory.  Every loop is bounded.
 #include "cplx.cuh"
 #include "kernels.cuh"
 #include "wd_internal.h"
@@ -242,6 +245,16 @@ __host__ __device__ inline double2 *cyc_zg(double2 *work, int m, int k) {
 }
 __host__ __device__ inline double2 *cyc_tau(double2 *work, int m, int k) {
   return work + (size_t)2 * (m + 1) * (m + 1) + (size_t)2 * m * m;
+}
+// The harmonic Ritz matrix M (m x m, row-major) shares the Hessenberg slot
+// (the FP64 fallback reads it before it writes H there), the refined
+// eigenvectors (row q: the vector of estimate q) the reflector slot.
+__host__ __device__ inline double2 *cyc_mat(double2 *work, int m, int k) { return cyc_hess(work, m, k); }
+__host__ __device__ inline double2 *cyc_vec(double2 *work, int m, int k) { return cyc_zg(work, m, k); }
+// [0, m): FP32 eigenvalue estimates; [m, 2m): refined eigenvalues; [2m, 3m):
+// relative residuals (.x); [3m]: (largest |M_ij|, 0); [3m + 1]: trace M
+__host__ __device__ inline double2 *cyc_est(double2 *work, int m, int k) {
+  return work + (size_t)2 * (m + 1) * (m + 1) + (size_t)2 * m * m + m;
 }
 
 // One thread per line (column of X from the left, row of Y from the right):
@@ -703,15 +716,446 @@ __device__ int schur_block(double2 *A, int m, int ld, double2 *u, long long *clk
   return 0;
 }
 
+// ----------------------------------------------------------------- eigenvalue estimates in FP32
+//
+// The cycle end needs every eigenvalue of the m x m harmonic Ritz matrix M
+// (to keep the k smallest) and the eigenvectors of the kept ones.  Its FP64
+// QR iteration is a chain of dependent FP64 instructions on one SM (64 clocks
+// each on this GPU).  Instead: all eigenvalues to FP32 accuracy by QR
+// iteration in FP32 (4-clock dependent arithmetic), then every estimate
+// refined in FP64 by inverse iteration with a Rayleigh-quotient update, one
+// CTA per estimate, on the original M.  The refined pairs are accepted only
+// when each has a residual of the order of rounding, the values are pairwise
+// distinct and they add up to the trace; otherwise the FP64 QR iteration runs
+// as before.
+
+__device__ __forceinline__ float2 fc_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 fc_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 fc_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 fc_conj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 fc_scale(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+__device__ __forceinline__ float2 fc_mul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float fc_abs1(float2 a) { return fabsf(a.x) + fabsf(a.y); }
+__device__ __forceinline__ float2 fc_div(float2 a, float2 b) {  // Smith's method
+  if (fabsf(b.x) >= fabsf(b.y)) {
+    const float r = b.y / b.x, d = b.x + r * b.y;
+    return make_float2((a.x + r * a.y) / d, (a.y - r * a.x) / d);
+  }
+  const float r = b.x / b.y, d = b.y + r * b.x;
+  return make_float2((r * a.x + a.y) / d, (r * a.y - a.x) / d);
+}
+__device__ __forceinline__ float2 fc_sqrt(float2 z) {  // principal square root
+  const float r = hypotf(z.x, z.y);
+  if (r == 0.f) return make_float2(0.f, 0.f);
+  const float w = sqrtf(0.5f * (r + fabsf(z.x)));
+  if (z.x >= 0.f) return make_float2(w, z.y / (2.f * w));
+  return make_float2(fabsf(z.y) / (2.f * w), copysignf(w, z.y));
+}
+
+// Sum of a float over the block, result in every thread (fixed order).
+__device__ float block_fsum_all(float v) {
+  __shared__ float sh[32];
+  __shared__ float res;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  __syncthreads();  // sh and res may still be read by a previous call
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.f;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+    if (threadIdx.x == 0) res = t;
+  }
+  __syncthreads();
+  return res;
+}
+
+// Largest value of a double over the block, result in every thread.
+__device__ double block_dmax_all(double v) {
+  __shared__ double sh[32];
+  __shared__ double res;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, off));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t = fmax(t, __shfl_down_sync(0xffffffffu, t, off));
+    if (threadIdx.x == 0) res = t;
+  }
+  __syncthreads();
+  return res;
+}
+
+// Householder reduction of the m x m FP32 matrix A (row-major, leading
+// dimension ld) to upper Hessenberg form, reflectors not kept (only the
+// eigenvalues are wanted).  As in the FP64 reduction, reflector j spans rows
+// j+1 .. iend, iend the last nonzero row of column j (a shared atomic
+// maximum, triple-buffered).  u: m scratch entries.  Block-wide.
+__device__ void hess_reduce_f32(float2 *A, int m, int ld, float2 *u) {
+  const int tid = threadIdx.x, bd = blockDim.x;
+  __shared__ int s_end[3];
+  if (tid < 3) s_end[tid] = 0;
+  __syncthreads();
+  for (int j = 0; j + 2 < m; ++j) {
+    const int slot = j % 3;
+    float part = 0.f;
+    for (int i = j + 2 + tid; i < m; i += bd) {
+      const float2 d = A[i * ld + j];
+      part = fmaf(d.x, d.x, fmaf(d.y, d.y, part));
+      if (d.x != 0.f || d.y != 0.f) atomicMax(&s_end[slot], i);
+    }
+    const float below = block_fsum_all(part);  // its barriers order the atomics
+    const int iend = s_end[slot];
+    if (tid == 0) s_end[(j + 2) % 3] = 0;
+    if (below == 0.f) continue;
+    const float2 al = A[(j + 1) * ld + j];
+    const float aa = hypotf(al.x, al.y), nx = sqrtf(below + aa * aa);
+    const float2 ph = aa > 0.f ? fc_scale(1.f / aa, al) : make_float2(1.f, 0.f);
+    const float2 beta = fc_scale(-nx, ph);
+    for (int i = j + 1 + tid; i <= iend; i += bd) u[i] = i == j + 1 ? fc_sub(al, beta) : A[i * ld + j];
+    __syncthreads();
+    const float tau = 1.f / (nx * (nx + aa));
+    // from the left on columns j+1 .. m-1 (column j is set below)
+    for (int c = j + 1 + tid; c < m; c += bd) {
+      float2 sd = make_float2(0.f, 0.f);
+      for (int i = j + 1; i <= iend; ++i) {
+        const float2 ui = u[i], x = A[i * ld + c];
+        sd.x = fmaf(ui.x, x.x, fmaf(ui.y, x.y, sd.x));
+        sd.y = fmaf(ui.x, x.y, fmaf(-ui.y, x.x, sd.y));
+      }
+      const float2 f = fc_scale(tau, sd);
+      for (int i = j + 1; i <= iend; ++i) A[i * ld + c] = fc_sub(A[i * ld + c], fc_mul(u[i], f));
+    }
+    __syncthreads();
+    // from the right on every row; column j of rows j+1 .. iend becomes (beta, 0, ...)
+    for (int r = tid; r < m; r += bd) {
+      float2 sd = make_float2(0.f, 0.f);
+      for (int i = j + 1; i <= iend; ++i) {
+        const float2 ui = u[i], x = A[r * ld + i];
+        sd.x = fmaf(x.x, ui.x, fmaf(-x.y, ui.y, sd.x));
+        sd.y = fmaf(x.x, ui.y, fmaf(x.y, ui.x, sd.y));
+      }
+      const float2 f = fc_scale(tau, sd);
+      for (int i = j + 1; i <= iend; ++i) A[r * ld + i] = fc_sub(A[r * ld + i], fc_mul(f, fc_conj(u[i])));
+      if (r > j && r <= iend) A[r * ld + j] = r == j + 1 ? beta : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+  }
+}
+
+// Eigenvalues of the upper Hessenberg FP32 matrix A by complex single-shift
+// QR iteration (the shift: the eigenvalue of the trailing 2 x 2 block nearer
+// its last diagonal entry; an exceptional shift every tenth sweep), rotations
+// applied inside the active window [l, hi] only (only eigenvalues are
+// wanted).  Threads 0 .. QR32_THREADS-1 call it (m <= QR32_THREADS): warp 0
+// scans for deflation and forms the shift; then each rotation takes one
+// matrix entry per thread, its row update and its column update separated
+// by a barrier of these threads.  The rotation's inputs (the entries of
+// column kk-1 in rows kk, kk+1) are passed through a double-buffered shared
+// slot by the threads that computed them, so no thread reads an entry that
+// another may be overwriting.  Eigenvalues end on the diagonal.  Returns 1
+// (every calling thread) if 30 m sweeps did not converge.
+constexpr int QR32_THREADS = 96;
+static_assert(QR32_THREADS >= CE_MAXM && QR32_THREADS % 32 == 0, "one thread per entry of a row or column");
+
+__device__ __forceinline__ void qr32_bar() {
+  asm volatile("bar.sync 1, %0;" ::"n"(QR32_THREADS) : "memory");
+}
+
+__device__ int qr_eig_f32(float2 *A, int m, int ld, long long *clk) {
+  const int t = threadIdx.x, lane = t & 31;
+  __shared__ int s_l[2];
+  __shared__ float2 s_xy[2][2];   // [step parity][x, y] of the next rotation
+  __shared__ float s_anorm;
+  if (t < 32) {
+    float an = 0.f;
+    for (int e = lane; e < m * m; e += 32) an = fmaxf(an, fc_abs1(A[(e / m) * ld + e % m]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) an = fmaxf(an, __shfl_xor_sync(0xffffffffu, an, off));
+    if (lane == 0) s_anorm = an > 0.f ? an : 1.f;
+  }
+  int hi = m - 1, its = 0, total = 0, scan = 0;
+  long long rotations = 0;
+  qr32_bar();
+  while (hi > 0) {
+    if (total >= 30 * m) return 1;                   // uniform
+    const int sp = scan & 1;
+    ++scan;
+    if (t < 32) {
+      // l = the largest index in [1, hi] whose subdiagonal entry is negligible
+      const float anorm = s_anorm;
+      int l = 0;
+      for (int q0 = 1; q0 <= hi; q0 += 32) {
+        const int q = q0 + lane;
+        bool neg = false;
+        if (q <= hi) {
+          float tst = fc_abs1(A[(q - 1) * ld + q - 1]) + fc_abs1(A[q * ld + q]);
+          if (tst == 0.f) tst = anorm;
+          neg = fc_abs1(A[q * ld + q - 1]) <= 1.1920929e-7f * tst;
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, neg);
+        if (b != 0u) l = q0 + 31 - __clz((int)b);
+      }
+      if (l != hi) {
+        // shift, and the first rotation's inputs (read by every lane before
+        // lane 0 writes anything)
+        const float2 a0 = A[(hi - 1) * ld + hi - 1], b0 = A[(hi - 1) * ld + hi];
+        const float2 c0 = A[hi * ld + hi - 1], d0 = A[hi * ld + hi];
+        float2 mu;
+        if ((its + 1) % 10 == 0) {
+          mu = fc_add(d0, make_float2(fc_abs1(c0), 0.f));
+        } else {
+          const float2 p = fc_scale(0.5f, fc_sub(a0, d0));
+          const float2 bc = fc_mul(b0, c0);
+          float2 q = fc_sqrt(fc_add(fc_mul(p, p), bc));
+          if (p.x * q.x + p.y * q.y < 0.f) q = fc_neg(q);
+          const float2 den = fc_add(p, q);
+          mu = (den.x == 0.f && den.y == 0.f) ? d0 : fc_sub(d0, fc_div(bc, den));
+        }
+        const float2 x = fc_sub(A[l * ld + l], mu), y = A[(l + 1) * ld + l];
+        if (lane == 0) {
+          s_xy[0][0] = x;
+          s_xy[0][1] = y;
+        }
+      }
+      if (lane == 0) {
+        if (l > 0) A[l * ld + l - 1] = make_float2(0.f, 0.f);
+        s_l[sp] = l;
+      }
+    }
+    qr32_bar();
+    const int l = s_l[sp];
+    if (l == hi) {
+      --hi;
+      its = 0;
+      continue;
+    }
+    ++its;
+    ++total;
+    for (int kk = l; kk < hi; ++kk) {
+      const int p = (kk - l) & 1;
+      const float2 x = s_xy[p][0], y = s_xy[p][1];
+      // G = [[c, s], [-conj(s), c]], G [x; y] = [r; 0] (every thread the same)
+      float c;
+      float2 s;
+      const float a2 = fmaf(x.x, x.x, x.y * x.y), b2 = fmaf(y.x, y.x, y.y * y.y);
+      if (a2 == 0.f) {
+        c = 0.f;
+        s = make_float2(1.f, 0.f);
+      } else {
+        const float ra = rsqrtf(a2), rn = rsqrtf(a2 + b2);
+        c = a2 * ra * rn;
+        s = fc_scale(ra * rn, fc_mul(x, fc_conj(y)));
+      }
+      // rows kk, kk+1 on columns c0 .. hi (the bulge (kk+1, kk-1) becomes 0)
+      const int c0 = kk > l ? kk - 1 : l;
+      const int j = c0 + t;
+      if (j <= hi) {
+        const float2 a1 = A[kk * ld + j], a3 = A[(kk + 1) * ld + j];
+        A[kk * ld + j] = fc_add(fc_scale(c, a1), fc_mul(s, a3));
+        A[(kk + 1) * ld + j] = (kk > l && j == kk - 1)
+                                   ? make_float2(0.f, 0.f)
+                                   : fc_sub(fc_scale(c, a3), fc_mul(fc_conj(s), a1));
+      }
+      qr32_bar();
+      // columns kk, kk+1 on rows l .. min(kk+2, hi); rows kk+1 and kk+2 of
+      // column kk are the next rotation's inputs
+      const int r1 = kk + 2 < hi ? kk + 2 : hi;
+      const int r = l + t;
+      if (r <= r1) {
+        const float2 a1 = A[r * ld + kk], a3 = A[r * ld + kk + 1];
+        const float2 n1 = fc_add(fc_scale(c, a1), fc_mul(fc_conj(s), a3));
+        A[r * ld + kk] = n1;
+        A[r * ld + kk + 1] = fc_sub(fc_scale(c, a3), fc_mul(s, a1));
+        if (kk + 1 < hi && r > kk) s_xy[p ^ 1][r - kk - 1] = n1;
+      }
+      qr32_bar();
+    }
+    rotations += hi - l;
+  }
+  if (clk != nullptr && t == 0) {
+    clk[8] = total;
+    clk[9] = rotations;
+  }
+  return 0;
+}
+
+// ----------------------------------------------------------------- banded LU in FP64
+//
+// After a GMRES-DR restart H_m is upper Hessenberg except for its full
+// leading (k+1) x k block, and so is M = H_m + |h|^2 f e_m^T (the last column
+// of a Hessenberg matrix is full anyway).  Gaussian elimination with partial
+// pivoting then only involves, in column j, rows j .. last[j], last[j] the
+// largest last-nonzero row of columns 0 .. j (fill stays inside it).
+
+// last[c] = max over columns c' <= c of the last row with a nonzero entry
+// in column c' (at least c').  Block-wide; ends with a barrier.
+__device__ void column_pattern(const double2 *A, int ld, int m, int *last) {
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    int r = m - 1;
+    while (r > c) {
+      const double2 v = A[r * ld + c];
+      if (v.x != 0.0 || v.y != 0.0) break;
+      --r;
+    }
+    last[c] = r;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int c = 1; c < m; ++c) last[c] = max(last[c], last[c - 1]);
+  __syncthreads();
+}
+
+// In-place LU of A with partial pivoting inside the band: step j swaps rows
+// j and piv[j] (columns > j; the multipliers of earlier columns stay in
+// place) and eliminates rows j+1 .. last[j], keeping the multipliers below
+// the diagonal and 1 / pivot in rp[j].  A pivot that is exactly zero is
+// replaced by `tiny`.  Block-wide.
+__device__ void lu_banded_block(double2 *A, int ld, int m, const int *last, int *piv, double2 *rp,
+                                double tiny) {
+  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31;
+  for (int j = 0; j < m; ++j) {
+    const int lj = last[j];
+    if (tid < 32) {
+      // pivot: the largest |re| + |im| in rows j .. lj (ties: the smaller row)
+      double best = -1.0;
+      int bi = j;
+      for (int i = j + lane; i <= lj; i += 32) {
+        const double v = cabs1(A[i * ld + j]);
+        if (v > best) {
+          best = v;
+          bi = i;
+        }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, best, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        if (ov > best || (ov == best && oi < bi)) {
+          best = ov;
+          bi = oi;
+        }
+      }
+      const int p = bi;
+      double2 pv = A[p * ld + j];
+      if (pv.x == 0.0 && pv.y == 0.0) pv = make_double2(tiny, 0.0);
+      const double2 r = cdiv(make_double2(1.0, 0.0), pv);
+      const double2 ujj = A[j * ld + j];
+      __syncwarp();
+      // multipliers of rows j+1 .. lj after the swap (row p receives row j)
+      for (int i = j + 1 + lane; i <= lj; i += 32) A[i * ld + j] = cmul(i == p ? ujj : A[i * ld + j], r);
+      if (lane == 0) {
+        A[j * ld + j] = pv;
+        piv[j] = p;
+        rp[j] = r;
+      }
+    }
+    __syncthreads();
+    const int p = piv[j];
+    if (p != j)
+      for (int c = j + 1 + tid; c < m; c += bd) {
+        const double2 t0 = A[j * ld + c];
+        A[j * ld + c] = A[p * ld + c];
+        A[p * ld + c] = t0;
+      }
+    __syncthreads();
+    const int nr = lj - j, nc = m - j - 1;
+    for (int e = tid; e < nr * nc; e += bd) {
+      const int i = j + 1 + e / nc, c = j + 1 + e % nc;
+      A[i * ld + c] = csub(A[i * ld + c], cmul(A[i * ld + j], A[j * ld + c]));
+    }
+    __syncthreads();
+  }
+}
+
+// y <- A^{-1} y with the factors of lu_banded_block.  Every lane of one warp.
+__device__ void lu_banded_solve_warp(const double2 *A, int ld, int m, const int *last,
+                                     const int *piv, const double2 *rp, double2 *y) {
+  const int lane = threadIdx.x & 31;
+  for (int j = 0; j + 1 < m; ++j) {
+    const int p = piv[j];
+    double2 yj = y[j];
+    if (p != j) {
+      const double2 yp = y[p];
+      __syncwarp();
+      if (lane == 0) {
+        y[p] = yj;
+        y[j] = yp;
+      }
+      yj = yp;
+      __syncwarp();
+    }
+    for (int i = j + 1 + lane; i <= last[j]; i += 32) y[i] = csub(y[i], cmul(A[i * ld + j], yj));
+    __syncwarp();
+  }
+  for (int j = m - 1; j >= 0; --j) {
+    const double2 yj = cmul(y[j], rp[j]);
+    __syncwarp();
+    if (lane == 0) y[j] = yj;
+    for (int i = lane; i < j; i += 32) y[i] = csub(y[i], cmul(A[i * ld + j], yj));
+    __syncwarp();
+  }
+}
+
+// w <- A^{-dagger} w with the same factors.  Elimination wrote
+// U = E_{m-2} S_{m-2} ... E_0 S_0 A (S_j the swap, E_j = I - l_j e_j^T), so
+// A^dagger w' = w is solved by U^dagger g = w (forward substitution), then
+// for j = m-2 .. 0: g_j -= l_j^dagger g (E_j^dagger), swap g_j, g_piv[j].
+// Every lane of one warp.
+__device__ void lu_banded_solve_adj_warp(const double2 *A, int ld, int m, const int *last,
+                                         const int *piv, const double2 *rp, double2 *w) {
+  const int lane = threadIdx.x & 31;
+  for (int j = 0; j < m; ++j) {
+    const double2 wj = cmul(w[j], cconj(rp[j]));   // w_j / conj(u_jj)
+    __syncwarp();
+    if (lane == 0) w[j] = wj;
+    for (int i = j + 1 + lane; i < m; i += 32) w[i] = csub(w[i], cmulc(A[j * ld + i], wj));
+    __syncwarp();
+  }
+  for (int j = m - 2; j >= 0; --j) {
+    double2 sd = make_double2(0.0, 0.0);
+    for (int i = j + 1 + lane; i <= last[j]; i += 32) sd = cfmac(A[i * ld + j], w[i], sd);
+    sd = warp_csum_all(sd);
+    const int p = piv[j];
+    const double2 wj = csub(w[j], sd), wp = w[p];
+    __syncwarp();
+    if (lane == 0) {
+      w[j] = p != j ? wp : wj;
+      if (p != j) w[p] = wj;
+    }
+    __syncwarp();
+  }
+}
+
+// y <- y / ||y||_2.  Every lane of one warp.
+__device__ void warp_normalize(double2 *y, int m) {
+  const int lane = threadIdx.x & 31;
+  double n2 = 0.0;
+  for (int i = lane; i < m; i += 32) n2 += cnorm2(y[i]);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, off);
+  const double inv = n2 > 0.0 ? rsqrt(n2) : 1.0;
+  for (int i = lane; i < m; i += 32) y[i] = cscale(inv, y[i]);
+  __syncwarp();
+}
+
 __global__ void __launch_bounds__(CE_THREADS) gmresdr_cycle_end_kernel(CycleEndArgs a) {
   extern __shared__ double2 sm[];
-  __shared__ int sel[CE_MAXM];
-  __shared__ int piv[CE_MAXM];
+  __shared__ int piv[CE_MAXM], last[CE_MAXM];
+  __shared__ double2 rp[CE_MAXM];
+  __shared__ int s_fail;
   const int m = a.m, k = a.k, tid = threadIdx.x, bd = blockDim.x;
   const int me = *a.m_eff;
   if (tid == 0) {
     a.flags[0] = 0;
     a.flags[1] = me < m ? 1 : 0;
+    a.flags[2] = 0;
   }
 #define STAMP(i) \
   if (a.clk != nullptr && tid == 0) a.clk[i] = clock64();
@@ -730,40 +1174,151 @@ __global__ void __launch_bounds__(CE_THREADS) gmresdr_cycle_end_kernel(CycleEndA
   // leading dimension = 1 mod 8 complex numbers: row-strided (column) access
   // by consecutive threads then walks all shared-memory banks
   const int ld = cyc_ld(m);
-  double2 *A = sm;               // m x ld
-  double2 *Z = A + m * ld;       // m x ld
+  double2 *A = sm;               // m x ld: H_m, then M
+  double2 *Z = A + m * ld;       // m x ld: LU of H_m, then the FP32 copy of M
   double2 *v1 = Z + m * ld;      // m+1
   double2 *v2 = v1 + (m + 1);    // m+1
-  // harmonic Ritz matrix H_m + |h_{m+1,m}|^2 f e_m^T with H_m^dagger f = e_m
+  // harmonic Ritz matrix M = H_m + |h_{m+1,m}|^2 f e_m^T with H_m^dagger f = e_m
+  double hmax = 0.0;
   for (int e = tid; e < m * m; e += bd) {
     const int i = e / m, j = e % m;
-    A[i * ld + j] = a.H[i * m + j];
-    Z[j * ld + i] = cconj(a.H[i * m + j]);
+    const double2 h = a.H[i * m + j];
+    A[i * ld + j] = h;
+    Z[i * ld + j] = h;
+    hmax = fmax(hmax, cabs1(h));
   }
   for (int i = tid; i < m; i += bd) v1[i] = make_double2(i == m - 1 ? 1.0 : 0.0, 0.0);
+  hmax = block_dmax_all(hmax);
+  column_pattern(Z, ld, m, last);
+  lu_banded_block(Z, ld, m, last, piv, rp, 2.220446049250313e-16 * (hmax > 0.0 ? hmax : 1.0));
+  if (tid < 32) lu_banded_solve_adj_warp(Z, ld, m, last, piv, rp, v1);
   __syncthreads();
-  lu_factor_block(Z, ld, m, piv);
-  __syncthreads();
-  lu_solve_block(Z, ld, piv, m, v1, 1, 1);
   STAMP(2)
   const double hh = cnorm2(a.H[m * m + m - 1]);
   for (int i = tid; i < m; i += bd) A[i * ld + m - 1] = cadd(A[i * ld + m - 1], cscale(hh, v1[i]));
   __syncthreads();
-  if (schur_block(A, m, ld, v2, a.clk, cyc_hess(a.work, m, k), cyc_zg(a.work, m, k),
-                  cyc_tau(a.work, m, k))) {
-    if (tid == 0) a.flags[0] = 1;
-    return;
+  // M to the work buffer (for the refinement and the FP64 fallback), with its
+  // largest entry and its trace
+  double2 *Mg = cyc_mat(a.work, m, k);
+  double2 *est = cyc_est(a.work, m, k);
+  double mmax = 0.0;
+  double2 tpart = make_double2(0.0, 0.0);
+  for (int e = tid; e < m * m; e += bd) {
+    const int i = e / m, j = e % m;
+    const double2 v = A[i * ld + j];
+    Mg[e] = v;
+    mmax = fmax(mmax, cabs1(v));
+    if (i == j) tpart = cadd(tpart, v);
+  }
+  mmax = block_dmax_all(mmax);
+  const double2 tr = block_csum_all(tpart);
+  if (tid == 0) {
+    est[3 * m] = make_double2(mmax, 0.0);
+    est[3 * m + 1] = tr;
+  }
+  // FP32 copy scaled by a power of two (entries below 1 in magnitude)
+  int ex = 0;
+  frexp(mmax > 0.0 ? mmax : 1.0, &ex);
+  const double sc = ldexp(1.0, -ex);
+  float2 *A32 = reinterpret_cast<float2 *>(Z);
+  for (int e = tid; e < m * m; e += bd) {
+    const int i = e / m, j = e % m;
+    const double2 v = A[i * ld + j];
+    A32[i * ld + j] = make_float2((float)(v.x * sc), (float)(v.y * sc));
   }
   __syncthreads();
+  hess_reduce_f32(A32, m, ld, reinterpret_cast<float2 *>(v2));
+  STAMP(7)
+  if (tid < QR32_THREADS) {
+    const int f = qr_eig_f32(A32, m, ld, a.clk);
+    if (tid == 0) s_fail = f;
+  }
+  __syncthreads();
+  if (s_fail) {
+    if (tid == 0) a.flags[2] = 1;      // estimates failed: the FP64 iteration runs
+  } else {
+    const double isc = 1.0 / sc;
+    for (int i = tid; i < m; i += bd) {
+      const float2 t = A32[i * ld + i];
+      est[i] = make_double2((double)t.x * isc, (double)t.y * isc);
+    }
+  }
   STAMP(3)
-  // order eigenvalues by (|theta|, Re, Im), index as the final tie-break
-  for (int i = tid; i < m; i += bd) {
-    const double2 ti = A[i * ld + i];
-    const double ai = cabs_(ti);
+#undef STAMP
+}
+
+// Refinement of eigenvalue estimate q of M (one CTA per estimate): two passes
+// of inverse iteration, each an LU of M - sigma I (banded) and two solves from
+// the previous vector (b = (1, ..., 1) at first), then sigma = y^dagger M y
+// for the normalised y.  sigma starts at the FP32 estimate, accurate to
+// ~1e-7 ||M||, so the second pass starts from a shift accurate to the square
+// of that.  Writes the refined value, ||M y - sigma y|| / max |M_ij| and y.
+constexpr int HRR_THREADS = 256;
+
+__global__ void __launch_bounds__(HRR_THREADS) harmonic_ritz_refine_kernel(CycleEndArgs a) {
+  extern __shared__ double2 sm[];
+  __shared__ int piv[CE_MAXM], last[CE_MAXM];
+  __shared__ double2 rp[CE_MAXM];
+  const int m = a.m, k = a.k, q = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
+  if (*a.m_eff < m || a.flags[2] != 0) return;        // uniform
+  const int ld = cyc_ld(m);
+  double2 *U = sm;                   // m x ld
+  double2 *y = U + m * ld;           // m
+  double2 *z = y + m;                // m: M y
+  const double2 *Mg = cyc_mat(a.work, m, k);
+  double2 *est = cyc_est(a.work, m, k);
+  const double anorm = est[3 * m].x > 0.0 ? est[3 * m].x : 1.0;
+  double2 sigma = est[q];
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int e = tid; e < m * m; e += bd) {
+      const int i = e / m, j = e % m;
+      const double2 v = Mg[e];
+      U[i * ld + j] = i == j ? csub(v, sigma) : v;
+    }
+    if (pass == 0)
+      for (int i = tid; i < m; i += bd) y[i] = make_double2(1.0, 0.0);
+    __syncthreads();
+    if (pass == 0) column_pattern(U, ld, m, last);
+    lu_banded_block(U, ld, m, last, piv, rp, 2.220446049250313e-16 * anorm);
+    if (tid < 32)
+      for (int it = 0; it < 2; ++it) {
+        lu_banded_solve_warp(U, ld, m, last, piv, rp, y);
+        warp_normalize(y, m);
+      }
+    __syncthreads();
+    double2 part = make_double2(0.0, 0.0);
+    for (int i = tid; i < m; i += bd) {
+      double2 sd = make_double2(0.0, 0.0);
+      for (int j = 0; j < m; ++j) sd = cfma(Mg[i * m + j], y[j], sd);
+      z[i] = sd;
+      part = cfmac(y[i], sd, part);
+    }
+    sigma = block_csum_all(part);      // its barriers order z
+  }
+  double rpart = 0.0;
+  for (int i = tid; i < m; i += bd) rpart += cnorm2(csub(z[i], cmul(sigma, y[i])));
+  const double rn = sqrt(block_dsum_all(rpart));
+  if (tid == 0) {
+    est[m + q] = sigma;
+    est[2 * m + q] = make_double2(rn / anorm, 0.0);
+  }
+  double2 *Y = cyc_vec(a.work, m, k);
+  for (int i = tid; i < m; i += bd) Y[(size_t)q * m + i] = y[i];
+}
+
+// Order (|theta|, Re, Im, index) of the m values th: the ranks of the k
+// smallest into sel.  Block-wide; ends with a barrier.
+__device__ void select_smallest(const double2 *th, int m, int k, int *sel) {
+  __shared__ double s_abs[CE_MAXM];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) s_abs[i] = cabs_(th[i]);
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double2 ti = th[i];
+    const double ai = s_abs[i];
     int rank = 0;
     for (int j = 0; j < m; ++j) {
-      const double2 tj = A[j * ld + j];
-      const double aj = cabs_(tj);
+      const double2 tj = th[j];
+      const double aj = s_abs[j];
       const bool less = aj < ai || (aj == ai && (tj.x < ti.x || (tj.x == ti.x && (tj.y < ti.y ||
                                                    (tj.y == ti.y && j < i)))));
       rank += less ? 1 : 0;
@@ -771,12 +1326,83 @@ __global__ void __launch_bounds__(CE_THREADS) gmresdr_cycle_end_kernel(CycleEndA
     if (rank < k) sel[rank] = i;
   }
   __syncthreads();
-  for (int q = tid; q < k; q += bd) a.theta[q] = A[sel[q] * ld + sel[q]];
-#undef STAMP
 }
 
-// Eigenvector of the Hessenberg matrix H (global Hg, leading dimension m)
-// for the selected harmonic Ritz value theta_q, one CTA per q: LU of
+// Acceptance of the refined pairs and selection of the k smallest |theta|:
+// every relative residual <= 1e-10, the values pairwise farther apart than
+// 1e-9 max |M_ij| (two estimates refined to the same eigenvalue would leave
+// another one out), and their sum within 1e-8 m max |M_ij| of the trace.
+// Then theta and the vectors of the kept values (columns of G).  Otherwise
+// flags[2] = 2 and the FP64 QR iteration takes over.
+__global__ void __launch_bounds__(CE_THREADS) harmonic_ritz_select_kernel(CycleEndArgs a) {
+  __shared__ int sel[CE_MAXM];
+  __shared__ int s_bad;
+  const int m = a.m, k = a.k, tid = threadIdx.x, bd = blockDim.x;
+  if (*a.m_eff < m || a.flags[2] != 0) return;        // uniform
+  const double2 *est = cyc_est(a.work, m, k);
+  const double2 *th = est + m;
+  const double anorm = est[3 * m].x > 0.0 ? est[3 * m].x : 1.0;
+  const double sep2 = (1e-9 * anorm) * (1e-9 * anorm);
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  double2 part = make_double2(0.0, 0.0);
+  for (int i = tid; i < m; i += bd) {
+    const double2 ti = th[i];
+    bool bad = !(est[2 * m + i].x <= 1e-10);          // also a NaN residual
+    for (int j = 0; j < m; ++j)
+      if (j != i && cnorm2(csub(th[j], ti)) <= sep2) bad = true;
+    if (bad) atomicOr(&s_bad, 1);
+    part = cadd(part, ti);
+  }
+  const double2 sum = block_csum_all(part);           // its barriers order the atomics
+  const bool bad = s_bad != 0 || !(cabs_(csub(sum, est[3 * m + 1])) <= 1e-8 * m * anorm);
+  if (a.clk != nullptr && tid == 0) a.clk[12] = bad ? 1 : 0;
+  if (bad) {
+    if (tid == 0) a.flags[2] = 2;
+    return;
+  }
+  select_smallest(th, m, k, sel);
+  for (int q = tid; q < k; q += bd) a.theta[q] = th[sel[q]];
+  double2 *G = a.work;
+  const double2 *Y = cyc_vec(a.work, m, k);
+  for (int e = tid; e < m * k; e += bd) {
+    const int i = e / k, q = e % k;
+    G[e] = Y[(size_t)sel[q] * m + i];
+  }
+}
+
+// The FP64 path, when the estimates were not accepted: eigenvalues of M by
+// the FP64 QR iteration (schur_block), the k smallest into theta; their
+// vectors then come from harmonic_ritz_vector_kernel.
+__global__ void __launch_bounds__(CE_THREADS) gmresdr_eig64_kernel(CycleEndArgs a) {
+  extern __shared__ double2 sm[];
+  __shared__ int sel[CE_MAXM];
+  const int m = a.m, k = a.k, tid = threadIdx.x, bd = blockDim.x;
+  if (*a.m_eff < m || a.flags[2] == 0) return;        // uniform
+  const int ld = cyc_ld(m);
+  double2 *A = sm;               // m x ld
+  double2 *Z = A + m * ld;       // m x ld (unused here: the layout of the cycle end)
+  double2 *v1 = Z + m * ld;      // m+1
+  double2 *v2 = v1 + (m + 1);    // m+1
+  const double2 *Mg = cyc_mat(a.work, m, k);
+  for (int e = tid; e < m * m; e += bd) A[(e / m) * ld + e % m] = Mg[e];
+  __syncthreads();
+  // (schur_block writes H over M in the work buffer after reading it here)
+  if (schur_block(A, m, ld, v2, nullptr, cyc_hess(a.work, m, k), cyc_zg(a.work, m, k),
+                  cyc_tau(a.work, m, k))) {
+    if (tid == 0) a.flags[0] = 1;
+    return;
+  }
+  __syncthreads();
+  __shared__ double2 s_th[CE_MAXM];
+  for (int i = tid; i < m; i += bd) s_th[i] = A[i * ld + i];
+  __syncthreads();
+  select_smallest(s_th, m, k, sel);
+  for (int q = tid; q < k; q += bd) a.theta[q] = s_th[sel[q]];
+}
+
+// (FP64 path) Eigenvector of the Hessenberg matrix H (global Hg, leading
+// dimension m) for the selected harmonic Ritz value theta_q, one CTA per q: LU of
 // H - theta I with partial pivoting between the two rows each column
 // touches, two inverse-iteration solves from b = (1, ..., 1), then g = Z y
 // (Z the product of the reduction's stored reflectors), into column q of G
@@ -788,7 +1414,7 @@ constexpr int HRV_THREADS = 128;
 __global__ void __launch_bounds__(HRV_THREADS) harmonic_ritz_vector_kernel(CycleEndArgs a) {
   extern __shared__ double2 sm[];
   const int m = a.m, k = a.k, q = blockIdx.x, tid = threadIdx.x, bd = blockDim.x;
-  if (*a.m_eff < m || a.flags[0] != 0) return;        // uniform: no restart basis needed
+  if (*a.m_eff < m || a.flags[0] != 0 || a.flags[2] == 0) return;   // uniform: not needed
   const int ld = cyc_ld(m);
   double2 *U = sm;                   // m x ld: LU factors of H - theta I
   double2 *y = U + m * ld;           // m
@@ -991,26 +1617,43 @@ cudaError_t launch_gmresdr_cycle_end(const CycleEndArgs &a, cudaStream_t s) {
   if (a.m > CE_MAXM || a.m < 1 || a.k < 0 || a.k >= a.m) return cudaErrorInvalidValue;
   const size_t smem = gmresdr_cycle_end_smem(a.m);
   const size_t smem_vec = ((size_t)a.m * cyc_ld(a.m) + a.m) * sizeof(double2);
+  const size_t smem_ref = ((size_t)a.m * cyc_ld(a.m) + 2 * a.m) * sizeof(double2);
   static thread_local int attr_device = -1;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (attr_device != dev) {
-    e = cudaFuncSetAttribute(gmresdr_cycle_end_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)gmresdr_cycle_end_smem(CE_MAXM));
+    const int big = (int)gmresdr_cycle_end_smem(CE_MAXM);
+    e = cudaFuncSetAttribute(gmresdr_cycle_end_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(gmresdr_eig64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(harmonic_ritz_vector_kernel,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(((size_t)CE_MAXM * cyc_ld(CE_MAXM) + CE_MAXM) * sizeof(double2)));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(harmonic_ritz_refine_kernel,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(((size_t)CE_MAXM * cyc_ld(CE_MAXM) + 2 * CE_MAXM) * sizeof(double2)));
     if (e != cudaSuccess) return e;
     attr_device = dev;
   }
   gmresdr_cycle_end_kernel<<<1, CE_THREADS, smem, s>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess || !a.do_restart || a.k == 0) return e;
-  // harmonic Ritz vectors by inverse iteration, one CTA per kept value, then
-  // the restarted basis (both return at once after a lucky breakdown or a
-  // failed eigenvalue iteration)
+  // every FP32 estimate refined in FP64 (one CTA each), acceptance and
+  // selection; the FP64 QR iteration and its eigenvector kernel return at
+  // once unless the estimates were rejected; then the restarted basis (all
+  // return at once after a lucky breakdown or a failed eigenvalue iteration)
+  harmonic_ritz_refine_kernel<<<a.m, HRR_THREADS, smem_ref, s>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  harmonic_ritz_select_kernel<<<1, CE_THREADS, 0, s>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  gmresdr_eig64_kernel<<<1, CE_THREADS, smem, s>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   harmonic_ritz_vector_kernel<<<a.k, HRV_THREADS, smem_vec, s>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

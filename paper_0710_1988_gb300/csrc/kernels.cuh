@@ -170,8 +170,8 @@ struct CycleEndArgs {
   double2 *Hk;         // (k+1) x k row-major: P^dagger Hbar P_k
   double2 *ck;         // k+1: P^dagger rho
   double2 *theta;      // k harmonic Ritz values
-  int *flags;          // [0] eig failure, [1] lucky
-  double2 *work;       // scratch >= 2*(m+1)*(m+1) + 2*m*m + m complex
+  int *flags;          // [0] eig failure, [1] lucky, [2] FP32 estimates rejected (FP64 path)
+  double2 *work;       // scratch >= 2*(m+1)*(m+1) + 2*m*m + 4*m + 2 complex
   long long *clk;      // nullptr, or 10 slots: SM clock at phase boundaries, QR sweeps, rotations
   int do_restart;
 };

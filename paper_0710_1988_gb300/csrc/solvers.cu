@@ -257,10 +257,10 @@ int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, doubl
   double2 *ck = ar.take<double2>(k + 1);
   double2 *theta = ar.take<double2>(k > 0 ? k : 1);
   double2 *scal = ar.take<double2>(2);
-  int *flags = ar.take<int>(2);
+  int *flags = ar.take<int>(3);
   int *status = ar.take<int>(1);
   int *m_eff = ar.take<int>(1);
-  double2 *work = ar.take<double2>((size_t)2 * (m + 1) * (m + 1) + (size_t)2 * m * m + m);
+  double2 *work = ar.take<double2>((size_t)2 * (m + 1) * (m + 1) + (size_t)2 * m * m + 4 * m + 2);
   // WD_TRACE_DENSE=1 prints the SM-clock split of every cycle-end kernel
   const bool trace_dense = std::getenv("WD_TRACE_DENSE") != nullptr;
   long long *clk = trace_dense ? ar.take<long long>(13) : nullptr;
@@ -338,11 +338,10 @@ int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, doubl
       WD_CK(cudaMemcpyAsync(hc, clk, sizeof(hc), cudaMemcpyDeviceToHost, s));
       WD_CK(cudaStreamSynchronize(s));
       std::fprintf(stderr,
-                   "cycle_end clk: lsq %lld lu %lld hessenberg %lld qr-iter %lld eigvec %lld "
-                   "qr(P) %lld products %lld | sweeps %lld rotations %lld scan %lld rot %lld "
-                   "tail %lld\n",
+                   "cycle_end clk: lsq %lld f %lld hessenberg32 %lld qr32 %lld refine %lld "
+                   "qr(P) %lld products %lld | qr32 sweeps %lld rotations %lld fp64 fallback %lld\n",
                    hc[1] - hc[0], hc[2] - hc[1], hc[7] - hc[2], hc[3] - hc[7], hc[4] - hc[3],
-                   hc[5] - hc[4], hc[6] - hc[5], hc[8], hc[9], hc[10], hc[11], hc[12]);
+                   hc[5] - hc[4], hc[6] - hc[5], hc[8], hc[9], hc[12]);
     }
     int hflags[2], hme;
     double hres;
