@@ -300,6 +300,18 @@ int wd_set_mixed_storage(wd_handle h, int bits);
  * 0: FP64 fused multiply-adds on the CUDA cores.  Other values: WD_BAD_ARG. */
 int wd_set_contraction(wd_handle h, int tensor_cores);
 
+/* How GMRES-DR's restart finds the harmonic Ritz pairs (Sec. 1: the
+ * eigenpairs of H_m + |h_{m+1,m}|^2 f e_m^T, the k of smallest modulus
+ * kept).  fp32_estimates = 1 (default): every eigenvalue estimated in FP32
+ * (Hessenberg reduction and shifted QR iteration), each refined in FP64 by
+ * inverse iteration on the matrix itself, one thread block per estimate;
+ * the refined pairs are used when each residual is at rounding level, the
+ * values are pairwise distinct and they sum to the trace, otherwise the
+ * next mode runs for that restart.  0: FP64 Hessenberg reduction and QR
+ * iteration, eigenvectors by inverse iteration on the Hessenberg form.
+ * Both give the pairs to FP64 rounding.  Other values: WD_BAD_ARG. */
+int wd_set_eigen_estimates(wd_handle h, int fp32_estimates);
+
 /* The tall-skinny product itself, without a handle (Sec. 1 restart, Sec. 2
  * projection updates): for c < ncol,
  *   OUT[c] = (beta_one ? IN[c] : 0) + sign * sum_{r < kv} V[r] Y[r*ldy + c],

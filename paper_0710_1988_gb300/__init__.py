@@ -186,6 +186,11 @@ class WilsonOperator:
         tensor cores (exact-split emulation, default) or in FP64 FMAs."""
         check(lib().wd_set_contraction(self._h, 1 if tensor_cores else 0))
 
+    def set_eigen_estimates(self, fp32: bool = True):
+        """GMRES-DR restart: harmonic Ritz pairs from FP32 estimates refined
+        in FP64 (default) or from the FP64 QR iteration alone."""
+        check(lib().wd_set_eigen_estimates(self._h, 1 if fp32 else 0))
+
     def gmresdr_history(self):
         """Least-squares residual / ||r0|| at the end of each cycle of the last
         gmresdr call on this operator (numpy float64 array)."""

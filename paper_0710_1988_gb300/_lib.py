@@ -73,6 +73,7 @@ SIGNATURES = {
     "wd_probe_fp64_peak": (I, [I, I, P, P, P]),
     "wd_probe_bf16_mma_peak": (I, [I, I, P, P, P]),
     "wd_set_contraction": (I, [P, I]),
+    "wd_set_eigen_estimates": (I, [P, I]),
     "wd_tsgemm": (I, [P, I, P, I, I, P, P, I, D, ctypes.c_longlong, I, P]),
     "wd_deflation_create": (I, [P, P, P, I, ctypes.POINTER(P), P]),
     "wd_deflation_destroy": (None, [P]),

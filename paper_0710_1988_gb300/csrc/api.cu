@@ -148,6 +148,7 @@ extern "C" int wd_create(const int lat[4], const void *links, double kappa, doub
   h->eo_tmp = nullptr;
   h->eo_tmp_cap = 0;
   h->tc_contract = 1;
+  h->eig32 = 1;
   for (int i = 0; i < 4; ++i) h->dims[i] = lat[i];
   h->V = V;
   h->n = 12 * V;
@@ -829,6 +830,13 @@ extern "C" int wd_set_contraction(wd_handle h, int tensor_cores) {
   if (h == nullptr) return bad("wd_set_contraction: NULL handle");
   if (tensor_cores != 0 && tensor_cores != 1) return bad("wd_set_contraction: 0 or 1");
   h->tc_contract = tensor_cores;
+  return WD_OK;
+}
+
+extern "C" int wd_set_eigen_estimates(wd_handle h, int fp32_estimates) {
+  if (h == nullptr) return bad("wd_set_eigen_estimates: NULL handle");
+  if (fp32_estimates != 0 && fp32_estimates != 1) return bad("wd_set_eigen_estimates: 0 or 1");
+  h->eig32 = fp32_estimates;
   return WD_OK;
 }
 

@@ -1215,7 +1215,9 @@ __global__ void __launch_bounds__(CE_THREADS) gmresdr_cycle_end_kernel(CycleEndA
   if (tid == 0) {
     est[3 * m] = make_double2(mmax, 0.0);
     est[3 * m + 1] = tr;
+    if (!a.eig32) a.flags[2] = 3;      // FP64 iteration requested
   }
+  if (!a.eig32) return;
   // FP32 copy scaled by a power of two (entries below 1 in magnitude)
   int ex = 0;
   frexp(mmax > 0.0 ? mmax : 1.0, &ex);

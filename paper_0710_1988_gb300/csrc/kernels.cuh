@@ -174,6 +174,7 @@ struct CycleEndArgs {
   double2 *work;       // scratch >= 2*(m+1)*(m+1) + 2*m*m + 4*m + 2 complex
   long long *clk;      // nullptr, or 10 slots: SM clock at phase boundaries, QR sweeps, rotations
   int do_restart;
+  int eig32;           // 1: FP32 estimates refined in FP64 first, 0: FP64 QR iteration only
 };
 cudaError_t launch_gmresdr_cycle_end(const CycleEndArgs &a, cudaStream_t s);
 size_t gmresdr_cycle_end_smem(int m);

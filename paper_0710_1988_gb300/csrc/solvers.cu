@@ -331,6 +331,7 @@ int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, doubl
     a.H = H; a.c = c; a.m = m; a.k = k; a.m_eff = m_eff; a.d = d; a.rho = rho; a.res = res;
     a.P = P; a.Hk = Hk; a.ck = ck; a.theta = theta; a.flags = flags; a.work = work;
     a.do_restart = 1;
+    a.eig32 = h->eig32;
     a.clk = clk;
     RET_IF(launch_ok(launch_gmresdr_cycle_end(a, s), "cycle_end"));
     if (clk) {

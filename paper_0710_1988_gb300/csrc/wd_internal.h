@@ -97,6 +97,7 @@ struct wd_context {
   size_t eo_tmp_cap;   // complex numbers
   std::vector<double> gmresdr_hist;  // last GMRES-DR solve: residual / ||r0|| per cycle
   int tc_contract;     // 1: wide V*Y products on the tensor cores (exact-split), 0: FP64
+  int eig32;           // 1: harmonic Ritz values from FP32 estimates refined in FP64, 0: FP64 QR
 };
 
 // Length (complex numbers) of the vectors the solvers work on.

@@ -4,6 +4,7 @@
     python -m paper_0710_1988_gb300.kernel_case --kernel f32 --even-odd --lattice 24 24 24 48 --nrhs 16
     python -m paper_0710_1988_gb300.kernel_case --kernel fp64-peak --reps 5
     python -m paper_0710_1988_gb300.kernel_case --kernel tsgemm --lattice 16 16 16 16 --kv 81 --ncol 41
+    python -m paper_0710_1988_gb300.kernel_case --kernel gmresdr --workload wilson_16x16x16x16
 
 Builds a seeded gauge field (U = exp(i 0.5 H)) and Gaussian spinors, then
 applies the operator `--reps` times through the public binding (`apply`,
@@ -26,12 +27,21 @@ def main(argv=None):
     from inputs import lattice as L
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", choices=["f64", "f32", "f16", "mixed", "fp64-peak", "tsgemm"],
+    ap.add_argument("--kernel", choices=["f64", "f32", "f16", "mixed", "fp64-peak", "tsgemm",
+                                         "gmresdr"],
                     default="f32",
                     help="a Wilson apply, 'mixed': --reps iterations of the FP32 mixed "
                          "BiCGStab on --nrhs sources (its vector updates and Wilson kernels), or "
                          "'fp64-peak': the library's DFMA throughput probe, 'tsgemm': the "
-                         "restart product V_{m+1} P_{k+1} (--kv, --ncol) in both forms")
+                         "restart product V_{m+1} P_{k+1} (--kv, --ncol) in both forms, "
+                         "'gmresdr': one GMRES-DR(m,k) solve of a workload's first source "
+                         "(--workload), its cycle-end kernels timed per restart")
+    ap.add_argument("--workload", default="wilson_16x16x16x16",
+                    help="a configuration of inputs.lattice (--kernel gmresdr)")
+    ap.add_argument("--kappa-c", type=float, default=None,
+                    help="kappa_c of the workload (default: the value stored with the tests)")
+    ap.add_argument("--fp64-eig", action="store_true",
+                    help="--kernel gmresdr: harmonic Ritz pairs by the FP64 QR iteration alone")
     ap.add_argument("--kv", type=int, default=81)
     ap.add_argument("--ncol", type=int, default=41)
     ap.add_argument("--lattice", type=int, nargs=4, default=[20, 20, 20, 32])
@@ -52,6 +62,38 @@ def main(argv=None):
             tf, ms = wdl.probe_bf16_mma_peak(iters=iters, reps=args.reps)
             print(json.dumps({"kernel": "bf16_mma_probe_kernel", "iters": iters, "reps": args.reps,
                               "tflops": tf, "ms_per_launch": ms}))
+        return
+    if args.kernel == "gmresdr":
+        cfg = L.CONFIGS[args.workload]
+        kc = args.kappa_c
+        if kc is None:
+            import os
+            path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                                "tests", "golden", "kappa_c.json")
+            with open(path) as f:
+                kc = json.load(f)[cfg.name]["kappa_c"]
+        kappa = cfg.kappa_factor * kc
+        U = L.gauge_field(cfg.dims, cfg.eps, L.link_seed(cfg))
+        b0 = torch.from_numpy(np.ascontiguousarray(L.source(cfg, 0)).reshape(-1)).cuda()
+        op = wdl.WilsonOperator(cfg.dims, torch.from_numpy(U).cuda(), kappa)
+        op.set_eigen_estimates(not args.fp64_eig)
+        V = torch.zeros(cfg.k * b0.numel(), dtype=torch.complex128, device="cuda")
+        res = []
+        for rep in range(2):          # the first solve warms up
+            x0 = torch.zeros_like(b0)
+            op.profile(mask=0x08)     # category 3: LU and the GMRES-DR cycle end
+            rc, st, _, theta = op.gmresdr(b0, x0, cfg.m, cfg.k, cfg.tol, 100000, V_out=V)
+            p = op.profile_read()
+            op.profile(mask=0)
+            res.append((rc, st, p["dense"]))
+        rc, st, dense = res[-1]
+        restarts = st["cycles"]
+        print(json.dumps({"kernel": "gmresdr_cycle_end", "workload": cfg.name, "m": cfg.m,
+                          "k": cfg.k, "fp32_estimates": not args.fp64_eig, "status": rc,
+                          "mvp": st["mvp"], "cycles": st["cycles"], "solve_ms": st["ms"],
+                          "cycle_end_launches": dense["launches"], "cycle_end_ms": dense["ms"],
+                          "ms_per_cycle_end": dense["ms"] / max(1, restarts)}))
+        op.close()
         return
     dims = tuple(args.lattice)
     if args.kernel == "tsgemm":
