@@ -8,8 +8,12 @@
 //    __half2 (re, im), scaled by a per-site norm  float [rhs][V]  (the largest
 //    |re| or |im| of the site), so every stored value lies in [-1, 1]:
 //    48 + 4 bytes per site.
-//  * half links   uint2 [mu][q][V], q = 0..2: rows 0 and 1 of U_mu, two
-//    complex numbers per uint2 (|u_ij| <= 1, no norm): 24 bytes per link.
+//  * half links   uint2 [mu][q][V], q = 0..4: the nine entries of U_mu row by
+//    row, two complex numbers per uint2 (the last one padded), |u_ij| <= 1, no
+//    norm: 40 bytes per link.  (Row 2 is stored rather than rebuilt as
+//    conj(row0 x row1): this kernel is bound by instruction issue, not by
+//    loads, so two more 8-byte loads cost less than the 27 arithmetic
+//    instructions of the rebuild.)
 #include <cuda_fp16.h>
 
 #include "cplx.cuh"
@@ -50,6 +54,22 @@ __device__ __forceinline__ float2 fcmul16(float2 a, float2 b) {
 __device__ __forceinline__ float2 f2of(double2 a) { return make_float2((float)a.x, (float)a.y); }
 
 }  // namespace
+
+// The stored half values of a site without its norm (the caller applies k).
+__device__ __forceinline__ float ld_h_raw(const uint4 *__restrict__ base,
+                                          const float *__restrict__ nrm, long long V, long long s,
+                                          float2 (&p)[12]) {
+  const float k = __ldg(nrm + s);
+#pragma unroll
+  for (int g = 0; g < 3; ++g) {
+    const uint4 q = __ldg(base + g * V + s);
+    p[4 * g] = h2f(q.x);
+    p[4 * g + 1] = h2f(q.y);
+    p[4 * g + 2] = h2f(q.z);
+    p[4 * g + 3] = h2f(q.w);
+  }
+  return k;
+}
 
 __device__ __forceinline__ void ld_h(const uint4 *__restrict__ base, const float *__restrict__ nrm,
                                      long long V, long long s, float2 (&p)[12]) {
@@ -100,27 +120,38 @@ __device__ __forceinline__ void st_f(float4 *__restrict__ base, long long V, lon
     base[g * V + s] = make_float4(p[2 * g].x, p[2 * g].y, p[2 * g + 1].x, p[2 * g + 1].y);
 }
 
+constexpr int LINK16_Q = 5;   // uint2 per FP16 link
+
 __device__ __forceinline__ void ld_link16(const uint2 *__restrict__ L, long long V, int mu,
                                           long long s, float2 (&u)[9]) {
-  const uint2 a = __ldg(L + (mu * 3 + 0) * V + s);
-  const uint2 b = __ldg(L + (mu * 3 + 1) * V + s);
-  const uint2 c = __ldg(L + (mu * 3 + 2) * V + s);
-  u[0] = h2f(a.x);
-  u[1] = h2f(a.y);
-  u[2] = h2f(b.x);
-  u[3] = h2f(b.y);
-  u[4] = h2f(c.x);
-  u[5] = h2f(c.y);
-  float2 t;
-  t = ssub(fcmul16(u[1], u[5]), fcmul16(u[2], u[4]));
-  u[6] = make_float2(t.x, -t.y);
-  t = ssub(fcmul16(u[2], u[3]), fcmul16(u[0], u[5]));
-  u[7] = make_float2(t.x, -t.y);
-  t = ssub(fcmul16(u[0], u[4]), fcmul16(u[1], u[3]));
-  u[8] = make_float2(t.x, -t.y);
+#pragma unroll
+  for (int q = 0; q < LINK16_Q; ++q) {
+    const uint2 a = __ldg(L + (mu * LINK16_Q + q) * V + s);
+    u[2 * q] = h2f(a.x);
+    if (2 * q + 1 < 9) u[2 * q + 1] = h2f(a.y);
+  }
 }
 
 // Input of the hop: a half vector, or (FUSED) r (FP32) - alpha v (half).
+// Returns the factor still to be applied: the site's norm for a plain half
+// vector (p holds its stored values; the hop scales its product once), 1
+// for the fused input (the norm is folded into alpha).
+template <bool FUSED>
+__device__ __forceinline__ float ld_hop16(const uint4 *__restrict__ in, const float *__restrict__ in_n,
+                                          const float4 *__restrict__ r32, float2 alpha, long long V,
+                                          long long s, float2 (&p)[12]) {
+  if (FUSED) {
+    float2 q[12];
+    ld_f(r32, V, s, p);
+    const float k = ld_h_raw(in, in_n, V, s, q);
+    const float2 ma = make_float2(-alpha.x * k, -alpha.y * k);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) p[c] = fcfma16(ma, q[c], p[c]);
+    return 1.f;
+  }
+  return ld_h_raw(in, in_n, V, s, p);
+}
+
 template <bool FUSED>
 __device__ __forceinline__ void ld_in16(const uint4 *__restrict__ in, const float *__restrict__ in_n,
                                         const float4 *__restrict__ r32, float2 alpha, long long V,
@@ -163,10 +194,15 @@ __device__ __forceinline__ void hop16(const uint2 *__restrict__ links, const Hal
   for (int r = 0; r < R; ++r) {
     if (!on[r]) continue;
     float2 p[12], h[6], c[6];
-    ld_in16<FUSED>(in.v + (long long)(r0 + r) * 3 * V, in.n + (long long)(r0 + r) * V,
-                   FUSED ? r32 + (long long)(r0 + r) * 6 * V : nullptr, alpha[r], V, q, p);
+    const float k = ld_hop16<FUSED>(in.v + (long long)(r0 + r) * 3 * V, in.n + (long long)(r0 + r) * V,
+                                    FUSED ? r32 + (long long)(r0 + r) * 6 * V : nullptr, alpha[r], V,
+                                    q, p);
     project<MU, S>(p, h);
     su3_mul16<ADJ>(u, h, c);
+    if (!FUSED) {
+#pragma unroll
+      for (int e = 0; e < 6; ++e) c[e] = make_float2(c[e].x * k, c[e].y * k);
+    }
     reconstruct<MU, S>(acc[r], c);
   }
 }
@@ -417,11 +453,11 @@ __global__ void links_to_f16_kernel(const double2 *__restrict__ U, uint2 *__rest
     for (int mu = 0; mu < 4; ++mu) {
       const double2 *u = U + (s * 4 + mu) * 9;
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
+      for (int q = 0; q < LINK16_Q; ++q) {
         uint2 w;
         w.x = f2h(f2of(u[2 * q]));
-        w.y = f2h(f2of(u[2 * q + 1]));
-        L[(mu * 3 + q) * V + s] = w;
+        w.y = 2 * q + 1 < 9 ? f2h(f2of(u[2 * q + 1])) : 0u;
+        L[(mu * LINK16_Q + q) * V + s] = w;
       }
     }
   }

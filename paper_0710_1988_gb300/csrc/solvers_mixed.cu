@@ -68,7 +68,7 @@ int ensure_links16(wd_context *h, cudaStream_t s) {
     return WD_BAD_ARG;
   }
   if (h->links16 != nullptr) return WD_OK;
-  WD_CK(cudaMalloc(&h->links16, sizeof(uint2) * 12 * h->V));
+  WD_CK(cudaMalloc(&h->links16, sizeof(uint2) * 20 * h->V));   // 4 links x 5 uint2
   WD_CK(launch_links_to_f16(h, h->links16, s));
   return WD_OK;
 }

@@ -79,7 +79,7 @@ struct wd_context {
   cudaMemPool_t pool;  // this handle's scratch pool
   wd::Profiler prof;   // optional kernel timing
   float4 *links32;     // FP32 rows 0, 1 of every link (mixed precision), lazily built
-  uint2 *links16;      // FP16 rows 0, 1 of every link, lazily built
+  uint2 *links16;      // FP16 links, all nine entries (5 uint2 per link), lazily built
   int mixed_bits;      // storage of the mixed solver's Krylov vectors: 32 or 16
   double mixed_delta;  // 0: reliable updates; > 0: restarted refinement (inner reduction)
   int mixed_inner_max; // restarted refinement: iterations before a forced restart
