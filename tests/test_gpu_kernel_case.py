@@ -32,3 +32,12 @@ def test_mixed_mode(extra):
     d = _run("--kernel", "mixed", "--lattice", "4", "4", "4", "8", "--nrhs", "2", "--reps", "20",
              *extra)
     assert d["iters"] == [20, 20] and d["ms"] > 0
+
+
+@pytest.mark.parametrize("extra", [[], ["--fp64-eig"]])
+def test_gmresdr_cycle_end_mode(extra):
+    """The cycle-end timing mode on the 4^4 workload (GMRES-DR(20,6)): both
+    eigenvalue paths converge with the same counts."""
+    d = _run("--kernel", "gmresdr", "--workload", "wilson_4x4x4x4", *extra)
+    assert d["status"] == 0 and d["fp32_estimates"] == (not extra)
+    assert d["cycle_end_launches"] == d["cycles"] and d["ms_per_cycle_end"] > 0
