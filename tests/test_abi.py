@@ -85,6 +85,8 @@ def test_new_entry_points_reject_bad_arguments_without_a_gpu(lib):
     assert lib.gmresdr_history(None, None, 0) == -_lib.WD_BAD_ARG
     # wd_set_contraction: NULL handle
     assert lib.wd_set_contraction(None, 1) == _lib.WD_BAD_ARG
+    # wd_set_eigen_estimates: NULL handle
+    assert lib.wd_set_eigen_estimates(None, 1) == _lib.WD_BAD_ARG
     # probes: bad sizes
     out = ctypes.c_double()
     assert lib.wd_probe_fp64_peak(0, 1, ctypes.byref(out), None, None) == _lib.WD_BAD_ARG
