@@ -37,7 +37,7 @@ def _solve(wdl, cfg, U, kappa, b0, B, fp32, m, k):
     return out
 
 
-@pytest.mark.parametrize("m,k", [(20, 6), (40, 12)])
+@pytest.mark.parametrize("m,k", [(20, 6), (40, 12), (80, 40)])
 def test_fp32_estimates_and_fp64_iteration_agree(wdl, m, k):
     from inputs import lattice as L
     from oracle import krylov
