@@ -363,6 +363,40 @@ int ts_dot_blocks(long long n, int k, int nrhs) {
   return (int)(g.x * g.y * g.z);
 }
 
+// Block reduction of a tile of 16 complex sums (32 doubles per thread) in a
+// fixed order, written as the block's partials.  Within a warp the 32
+// doubles are reduced by recursive halving: at each of the five levels a
+// lane keeps half of its values, sends the other half to its partner and
+// adds what it receives, so lane i ends with the warp sum of value i after
+// 16 + 8 + 4 + 2 + 1 additions (a shuffle tree per value would take 160).
+template <int Q = 16>   // complex sums of the tile written (the first Q of the 16)
+__device__ __forceinline__ void ts_tile_reduce(double (&vals)[32], double2 *__restrict__ partial) {
+  __shared__ double red[32][TS_THREADS / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int lvl = 0; lvl < 5; ++lvl) {
+    const int half = 16 >> lvl;           // values kept after this level
+    const bool upper = (lane >> (4 - lvl)) & 1;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const double send = upper ? vals[i] : vals[i + half];
+      const double keep = upper ? vals[i + half] : vals[i];
+      vals[i] = keep + __shfl_xor_sync(0xffffffffu, send, half);
+    }
+  }
+  red[lane][wid] = vals[0];
+  __syncthreads();
+  const long long tile = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  for (int q = threadIdx.x; q < Q; q += blockDim.x) {
+    double a = 0.0, b = 0.0;
+    for (int w2 = 0; w2 < TS_THREADS / 32; ++w2) {
+      a += red[q * 2][w2];
+      b += red[q * 2 + 1][w2];
+    }
+    partial[tile * Q + q] = make_double2(a, b);
+  }
+}
+
 template <int JT, int RT>
 __global__ void __launch_bounds__(TS_THREADS)
 ts_dot_kernel(const double2 *__restrict__ V, int k, const double2 *__restrict__ W, int nrhs,
@@ -394,14 +428,6 @@ ts_dot_kernel(const double2 *__restrict__ V, int k, const double2 *__restrict__ 
       }
     }
   }
-  // Block reduction of the tile, fixed order.  Within a warp the 32 doubles
-  // of the tile are reduced by recursive halving: at each of the five levels
-  // a lane keeps half of its values, sends the other half to its partner and
-  // adds what it receives, so lane i ends with the warp sum of value i after
-  // 16 + 8 + 4 + 2 + 1 additions (a shuffle tree per value would take 160).
-  static_assert(JT * RT * 2 == 32, "the tile holds 32 doubles");
-  __shared__ double red[32][TS_THREADS / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   double vals[32];
 #pragma unroll
   for (int j = 0; j < JT; ++j)
@@ -410,28 +436,8 @@ ts_dot_kernel(const double2 *__restrict__ V, int k, const double2 *__restrict__ 
       vals[(j * RT + r) * 2] = acc[j][r].x;
       vals[(j * RT + r) * 2 + 1] = acc[j][r].y;
     }
-#pragma unroll
-  for (int lvl = 0; lvl < 5; ++lvl) {
-    const int half = 16 >> lvl;           // values kept after this level
-    const bool upper = (lane >> (4 - lvl)) & 1;
-#pragma unroll
-    for (int i = 0; i < half; ++i) {
-      const double send = upper ? vals[i] : vals[i + half];
-      const double keep = upper ? vals[i + half] : vals[i];
-      vals[i] = keep + __shfl_xor_sync(0xffffffffu, send, half);
-    }
-  }
-  red[lane][wid] = vals[0];
-  __syncthreads();
-  const long long tile = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  for (int q = threadIdx.x; q < JT * RT; q += blockDim.x) {
-    double a = 0.0, b = 0.0;
-    for (int w2 = 0; w2 < TS_THREADS / 32; ++w2) {
-      a += red[q * 2][w2];
-      b += red[q * 2 + 1][w2];
-    }
-    partial[tile * JT * RT + q] = make_double2(a, b);
-  }
+  static_assert(JT * RT * 2 == 32, "the tile holds 32 doubles");
+  ts_tile_reduce(vals, partial);
 }
 
 // One warp per (j, r) pair: the lanes load the gx block partials of the pair
@@ -477,6 +483,134 @@ cudaError_t launch_ts_dot(const double2 *V, int k, const double2 *W, int nrhs, i
     ts_dot_kernel<16, 1><<<grid, TS_THREADS, 0, s>>>(V, k, W, nrhs, g5, n, partial, status);
   else
     ts_dot_kernel<8, 2><<<grid, TS_THREADS, 0, s>>>(V, k, W, nrhs, g5, n, partial, status);
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------- first Gram-Schmidt pass, double-float
+
+// h = V^dagger w for one vector w with every product and sum carried as a
+// pair of FP32 numbers (about 48 significant bits), on this GPU's FP32 pipe
+// instead of its much slower FP64 one.  It serves the first pass of
+// classical Gram-Schmidt applied twice: the second pass, in FP64, measures
+// and removes whatever this one left (its coefficients h2 = V^dagger(w - V h)
+// are then of the order of 2^-48 ||w|| instead of 2^-53), and the Hessenberg
+// column h + h2 is exact to FP64 rounding.  An operand outside FP32's range
+// contributes nothing here and is removed by the FP64 pass.
+//  * split: x = hi + lo with hi the top 24 significant bits of x (bit
+//    operations, no FP64 instruction) and lo the next 24 (x - hi rounded).
+//  * product: Dekker's exact product by FMA, p + e = ah bh, plus the cross
+//    terms ah bl + al bh (al bl is below 2^-48 of the product).
+//  * sum: Knuth's TwoSum of the running high part and p; the rounding error
+//    and the low parts accumulate in the low word.
+__device__ __forceinline__ void split_df(double x, float &hi, float &lo) {
+  const long long b = __double_as_longlong(x);
+  const unsigned sign = (unsigned)((unsigned long long)b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7FF);
+  const int fe = e - 1023 + 127;
+  if (fe <= 0 || fe >= 255) {   // zero, or outside FP32's normal range
+    hi = 0.f;
+    lo = 0.f;
+    return;
+  }
+  hi = __uint_as_float(sign | ((unsigned)fe << 23) | ((unsigned)(b >> 29) & 0x7FFFFFu));
+  const unsigned rem = (unsigned)b & 0x1FFFFFFFu;       // the 29 fraction bits below hi
+  if (rem == 0u || e < 949) {                            // nothing left, or 2^(e-1075) underflows
+    lo = 0.f;
+    return;
+  }
+  const float scale = __uint_as_float((unsigned)(e - 948) << 23);   // 2^(e - 1075)
+  lo = __uint_as_float(__float_as_uint(__uint2float_rn(rem) * scale) | sign);
+}
+
+__device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, float &sh,
+                                       float &sl) {
+  const float p = ah * bh;
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, fmaf(al, bh, e));
+  const float sum = sh + p;
+  const float t = sum - sh;
+  const float err = (sh - (sum - t)) + (p - t);
+  sl += err + e;
+  sh = sum;
+}
+
+// Tiles of DF_JT basis vectors: a tile's loads are issued together before
+// its arithmetic (the FP32 arithmetic is too quick to hide the loads the way
+// the FP64 pipe does in ts_dot_kernel), and the smaller tile leaves
+// registers for three blocks per SM.
+constexpr int DF_JT = 8;
+
+static void ts_dot_df_grid(long long n, int k, dim3 *grid) {
+  const int gy = (k + DF_JT - 1) / DF_JT;
+  long long gx = TS_MAX_BLOCKS / gy;
+  const long long need = (n + TS_THREADS - 1) / TS_THREADS;
+  if (gx > need) gx = need;
+  if (gx < 8) gx = need < 8 ? need : 8;
+  if (gx < 1) gx = 1;
+  *grid = dim3((unsigned)gx, gy, 1);
+}
+
+__global__ void __launch_bounds__(TS_THREADS, 3)
+ts_dot_df_kernel(const double2 *__restrict__ V, int k, const double2 *__restrict__ W, long long n,
+                 double2 *__restrict__ partial, const int *__restrict__ status) {
+  if (status != nullptr && *status != 0) return;
+  const int j0 = blockIdx.y * DF_JT;
+  const int nj = min(DF_JT, k - j0);
+  float arh[DF_JT], arl[DF_JT], aih[DF_JT], ail[DF_JT];
+#pragma unroll
+  for (int j = 0; j < DF_JT; ++j) arh[j] = arl[j] = aih[j] = ail[j] = 0.f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double2 v[DF_JT];
+#pragma unroll
+    for (int j = 0; j < DF_JT; ++j)   // rows past the last vector reread it and add nothing
+      v[j] = __ldg(V + (long long)(j0 + (j < nj ? j : nj - 1)) * n + i);
+    const double2 w = __ldg(W + i);
+    float wrh, wrl, wih, wil;
+    split_df(w.x, wrh, wrl);
+    split_df(w.y, wih, wil);
+#pragma unroll
+    for (int j = 0; j < DF_JT; ++j) {
+      float vrh, vrl, vih, vil;
+      split_df(v[j].x, vrh, vrl);
+      split_df(v[j].y, vih, vil);
+      if (j >= nj) vrh = vrl = vih = vil = 0.f;
+      // conj(v) w = (vr wr + vi wi) + i (vr wi - vi wr)
+      df_mac(vrh, vrl, wrh, wrl, arh[j], arl[j]);
+      df_mac(vih, vil, wih, wil, arh[j], arl[j]);
+      df_mac(vrh, vrl, wih, wil, aih[j], ail[j]);
+      df_mac(-vih, -vil, wrh, wrl, aih[j], ail[j]);
+    }
+  }
+  // the tile's DF_JT complex sums in the first 2 DF_JT of the 32 reduced values
+  double vals[32];
+#pragma unroll
+  for (int j = 0; j < DF_JT; ++j) {
+    vals[2 * j] = (double)arh[j] + (double)arl[j];
+    vals[2 * j + 1] = (double)aih[j] + (double)ail[j];
+  }
+#pragma unroll
+  for (int q = 2 * DF_JT; q < 32; ++q) vals[q] = 0.0;
+  ts_tile_reduce<DF_JT>(vals, partial);
+}
+
+cudaError_t launch_ts_dot_df(const double2 *V, int k, const double2 *w, long long n,
+                             double2 *partial, const int *status, cudaStream_t s) {
+  ProfLaunch prof_(PC_TS, s);
+  if (k < 1 || k > 4096) return cudaErrorInvalidValue;
+  dim3 grid;
+  ts_dot_df_grid(n, k, &grid);
+  ts_dot_df_kernel<<<grid, TS_THREADS, 0, s>>>(V, k, w, n, partial, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ts_dot_df_finalize(const double2 *partial, long long n, int k, double2 *C,
+                                      int ldc, const int *status, cudaStream_t s) {
+  ProfLaunch prof_(PC_TS, s);
+  dim3 grid;
+  ts_dot_df_grid(n, k, &grid);
+  ts_dot_finalize_kernel<<<(k + 3) / 4, 128, 0, s>>>(partial, grid.x, grid.y, DF_JT, 1, k, 1, C,
+                                                     ldc, nullptr, 0, status);
   return cudaGetLastError();
 }
 

@@ -111,6 +111,15 @@ cudaError_t launch_ts_dot(const double2 *V, int k, const double2 *W, int nrhs, i
 cudaError_t launch_ts_dot_finalize(const double2 *partial, long long n, int k, int nrhs,
                                    double2 *C, int ldc, double2 *C2, int ldc2,
                                    const int *status, cudaStream_t s);
+// launch_ts_dot for one vector (nrhs = 1, no gamma5) in double-float
+// arithmetic (about 48 bits, on the FP32 pipe): the first pass of CGS2, whose
+// error the FP64 second pass removes.  Its partials (at most
+// ts_dot_partial_count(n, k, 1)) are summed by launch_ts_dot_df_finalize
+// into C[j * ldc], j < k.
+cudaError_t launch_ts_dot_df(const double2 *V, int k, const double2 *w, long long n,
+                             double2 *partial, const int *status, cudaStream_t s);
+cudaError_t launch_ts_dot_df_finalize(const double2 *partial, long long n, int k, double2 *C,
+                                      int ldc, const int *status, cudaStream_t s);
 // OUT[c][i] = (beta_one ? IN[c][i] : 0) + sign * sum_j V[j][i] Y[j*ldy + c],
 // c < ncol, kv <= 128.  OUT may alias IN (in-place update) but not V.
 cudaError_t launch_ts_update(const double2 *V, int kv, const double2 *Y, int ldy, int ncol,

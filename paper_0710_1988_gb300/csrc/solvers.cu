@@ -314,9 +314,12 @@ int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, doubl
       double2 *vj = V + (size_t)j * n;
       // w = A v_j, with ||w||^2 fused (lucky-breakdown reference)
       RET_IF(launch_ok(launch_wilson_f64_epi(h, vj, w, 1, 0, EPI_TSTT, nullptr, part_w, status, s, M_ACTIVE), "arnoldi wilson"));
-      // classical Gram-Schmidt, applied twice
-      RET_IF(launch_ok(launch_ts_dot(V, j + 1, w, 1, 0, n, part_t, status, s), "cgs dot1"));
-      RET_IF(launch_ok(launch_ts_dot_finalize(part_t, n, j + 1, 1, H + j, m, nullptr, 0, status, s), "cgs fin1"));
+      // classical Gram-Schmidt, applied twice: the first pass's coefficients
+      // in double-float (~48 bits, FP32 pipe), the second pass's in FP64 (it
+      // removes what the first left, so H = h1 + h2 is exact to FP64
+      // rounding), its update in FP32 when h2 is at rounding level
+      RET_IF(launch_ok(launch_ts_dot_df(V, j + 1, w, n, part_t, status, s), "cgs dot1"));
+      RET_IF(launch_ok(launch_ts_dot_df_finalize(part_t, n, j + 1, H + j, m, status, s), "cgs fin1"));
       RET_IF(launch_ok(launch_ts_update(V, j + 1, H + j, m, 1, w, w, 1, -1.0, n, status, s), "cgs upd1"));
       RET_IF(launch_ok(launch_ts_dot(V, j + 1, w, 1, 0, n, part_t, status, s), "cgs dot2"));
       RET_IF(launch_ok(launch_ts_dot_finalize(part_t, n, j + 1, 1, h2, 1, H + j, m, status, s), "cgs fin2"));

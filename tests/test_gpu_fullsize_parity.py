@@ -59,13 +59,15 @@ def run():
     rc, st, hbar, theta = op.gmresdr(b0, torch.zeros_like(b0), cfg.m, cfg.k, cfg.tol, 400000,
                                      V_out=V)
     hist = op.gmresdr_history()
+    Vm = V.view(cfg.k, n)
+    orth = (Vm.conj() @ Vm.T - torch.eye(cfg.k, dtype=V.dtype, device=V.device)).abs().max().item()
     defl = op.deflation(V, cfg.k)
     Bh = np.stack([L.source(cfg, j).ravel() for j in range(1, cfg.n_rhs + 1)])
     X = cuda(np.zeros_like(Bh))
     rc2, sts = op.dbicgstab(cuda(Bh), X, defl, tol=cfg.tol)
     X11 = cuda(np.zeros_like(Bh[:1]))
     rc3, sts11 = op.dbicgstab(cuda(Bh[:1]), X11, defl, tol=1e-11)
-    out = dict(cfg=cfg, kappa=kappa, rc=rc, st=st, theta=theta, hbar=hbar, hist=hist,
+    out = dict(cfg=cfg, kappa=kappa, rc=rc, st=st, theta=theta, hbar=hbar, hist=hist, orth=orth,
                rc2=rc2, sts=sts, X=host(X), rc3=rc3, X11=host(X11)[0])
     defl.close()
     op.close()
@@ -81,6 +83,12 @@ def test_gmresdr_counts_and_history_match_oracle(run):
     hist, ho = np.asarray(run["hist"]), np.asarray(g["gmresdr_history"])
     assert hist.shape == ho.shape
     assert np.all(np.abs(hist - ho) <= 1e-4 * ho), np.abs(hist / ho - 1).max()
+
+
+def test_deflation_basis_is_orthonormal(run):
+    """V = V_{m+1} P_k after the last restart: orthonormal to FP64 rounding
+    (the first Gram-Schmidt pass runs in double-float, the second in FP64)."""
+    assert run["orth"] <= 1e-13, run["orth"]
 
 
 def test_harmonic_ritz_values_match_oracle(run):
