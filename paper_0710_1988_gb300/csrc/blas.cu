@@ -536,9 +536,11 @@ __device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, f
 
 // Tiles of DF_JT basis vectors: a tile's loads are issued together before
 // its arithmetic (the FP32 arithmetic is too quick to hide the loads the way
-// the FP64 pipe does in ts_dot_kernel), and the smaller tile leaves
-// registers for three blocks per SM.
-constexpr int DF_JT = 8;
+// the FP64 pipe does in ts_dot_kernel), and the small tile leaves registers
+// for four blocks per SM (63 registers, no spills): the kernel is bound by
+// instruction issue and latency, so occupancy pays (16^4 tall-skinny time per
+// step: 8-vector tiles at three blocks 477 ms, 4 at five 464, 4 at four 450).
+constexpr int DF_JT = 4;
 
 static void ts_dot_df_grid(long long n, int k, dim3 *grid) {
   const int gy = (k + DF_JT - 1) / DF_JT;
@@ -550,7 +552,7 @@ static void ts_dot_df_grid(long long n, int k, dim3 *grid) {
   *grid = dim3((unsigned)gx, gy, 1);
 }
 
-__global__ void __launch_bounds__(TS_THREADS, 3)
+__global__ void __launch_bounds__(TS_THREADS, 4)
 ts_dot_df_kernel(const double2 *__restrict__ V, int k, const double2 *__restrict__ W, long long n,
                  double2 *__restrict__ partial, const int *__restrict__ status) {
   if (status != nullptr && *status != 0) return;
