@@ -726,8 +726,9 @@ __device__ int schur_block(double2 *A, int m, int ld, double2 *u, long long *clk
 // refined in FP64 by inverse iteration with a Rayleigh-quotient update, one
 // CTA per estimate, on the original M.  The refined pairs are accepted only
 // when each has a residual of the order of rounding, the values are pairwise
-// distinct and they add up to the trace; otherwise the FP64 QR iteration runs
-// as before.
+// distinct and they add up to the trace; otherwise the FP64 Hessenberg
+// reduction and QR iteration (gmresdr_eig64_kernel) and inverse iteration on
+// the Hessenberg form (harmonic_ritz_vector_kernel) give them.
 
 __device__ __forceinline__ float2 fc_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 fc_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
