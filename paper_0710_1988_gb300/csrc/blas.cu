@@ -553,7 +553,7 @@ static void ts_dot_df_grid(long long n, int k, dim3 *grid) {
 }
 
 __global__ void __launch_bounds__(TS_THREADS, 4)
-ts_dot_df_kernel(const double2 *__restrict__ V, int k, const double2 *__restrict__ W, long long n,
+ts_dot_df_kernel(const float4 *__restrict__ V, int k, const double2 *__restrict__ W, long long n,
                  double2 *__restrict__ partial, const int *__restrict__ status) {
   if (status != nullptr && *status != 0) return;
   const int j0 = blockIdx.y * DF_JT;
@@ -563,7 +563,7 @@ ts_dot_df_kernel(const double2 *__restrict__ V, int k, const double2 *__restrict
   for (int j = 0; j < DF_JT; ++j) arh[j] = arl[j] = aih[j] = ail[j] = 0.f;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    double2 v[DF_JT];
+    float4 v[DF_JT];
 #pragma unroll
     for (int j = 0; j < DF_JT; ++j)   // rows past the last vector reread it and add nothing
       v[j] = __ldg(V + (long long)(j0 + (j < nj ? j : nj - 1)) * n + i);
@@ -573,9 +573,7 @@ ts_dot_df_kernel(const double2 *__restrict__ V, int k, const double2 *__restrict
     split_df(w.y, wih, wil);
 #pragma unroll
     for (int j = 0; j < DF_JT; ++j) {
-      float vrh, vrl, vih, vil;
-      split_df(v[j].x, vrh, vrl);
-      split_df(v[j].y, vih, vil);
+      float vrh = v[j].x, vrl = v[j].y, vih = v[j].z, vil = v[j].w;
       if (j >= nj) vrh = vrl = vih = vil = 0.f;
       // conj(v) w = (vr wr + vi wi) + i (vr wi - vi wr)
       df_mac(vrh, vrl, wrh, wrl, arh[j], arl[j]);
@@ -596,7 +594,33 @@ ts_dot_df_kernel(const double2 *__restrict__ V, int k, const double2 *__restrict
   ts_tile_reduce<DF_JT>(vals, partial);
 }
 
-cudaError_t launch_ts_dot_df(const double2 *V, int k, const double2 *w, long long n,
+// Each complex128 entry of v as (Re hi, Re lo, Im hi, Im lo) FP32: the basis
+// in the form the double-float dot reads, written once per basis vector.
+__global__ void __launch_bounds__(256)
+split_df_kernel(const double2 *__restrict__ v, float4 *__restrict__ vs, long long count,
+                const int *__restrict__ status) {
+  if (status != nullptr && *status != 0) return;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 a = v[i];
+    float4 o;
+    split_df(a.x, o.x, o.y);
+    split_df(a.y, o.z, o.w);
+    vs[i] = o;
+  }
+}
+
+cudaError_t launch_split_df(const double2 *v, float4 *vs, long long count, const int *status,
+                            cudaStream_t s) {
+  ProfLaunch prof_(PC_TS, s);
+  long long blocks = (count + 255) / 256;
+  if (blocks > 4 * 1216) blocks = 4 * 1216;
+  if (blocks < 1) blocks = 1;
+  split_df_kernel<<<(unsigned)blocks, 256, 0, s>>>(v, vs, count, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ts_dot_df(const float4 *V, int k, const double2 *w, long long n,
                              double2 *partial, const int *status, cudaStream_t s) {
   ProfLaunch prof_(PC_TS, s);
   if (k < 1 || k > 4096) return cudaErrorInvalidValue;

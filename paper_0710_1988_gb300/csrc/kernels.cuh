@@ -113,11 +113,16 @@ cudaError_t launch_ts_dot_finalize(const double2 *partial, long long n, int k, i
                                    const int *status, cudaStream_t s);
 // launch_ts_dot for one vector (nrhs = 1, no gamma5) in double-float
 // arithmetic (about 48 bits, on the FP32 pipe): the first pass of CGS2, whose
-// error the FP64 second pass removes.  Its partials (at most
+// error the FP64 second pass removes.  V in the split form of
+// launch_split_df (k vectors of n float4).  Its partials (at most
 // ts_dot_partial_count(n, k, 1)) are summed by launch_ts_dot_df_finalize
 // into C[j * ldc], j < k.
-cudaError_t launch_ts_dot_df(const double2 *V, int k, const double2 *w, long long n,
+cudaError_t launch_ts_dot_df(const float4 *V, int k, const double2 *w, long long n,
                              double2 *partial, const int *status, cudaStream_t s);
+// vs[i] = (Re hi, Re lo, Im hi, Im lo) of v[i] (FP32 pairs of ~48 bits; an
+// entry outside FP32's normal range gives zeros), i < count.
+cudaError_t launch_split_df(const double2 *v, float4 *vs, long long count, const int *status,
+                            cudaStream_t s);
 cudaError_t launch_ts_dot_df_finalize(const double2 *partial, long long n, int k, double2 *C,
                                       int ldc, const int *status, cudaStream_t s);
 // OUT[c][i] = (beta_one ? IN[c][i] : 0) + sign * sum_j V[j][i] Y[j*ldy + c],
