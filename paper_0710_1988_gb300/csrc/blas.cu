@@ -553,8 +553,9 @@ static void ts_dot_df_grid(long long n, int k, dim3 *grid) {
 }
 
 __global__ void __launch_bounds__(TS_THREADS, 4)
-ts_dot_df_kernel(const float4 *__restrict__ V, int k, const double2 *__restrict__ W, long long n,
-                 double2 *__restrict__ partial, const int *__restrict__ status) {
+ts_dot_df_kernel(const float2 *__restrict__ Vh, const float2 *__restrict__ Vl, int k,
+                 const double2 *__restrict__ W, long long n, double2 *__restrict__ partial,
+                 const int *__restrict__ status) {
   if (status != nullptr && *status != 0) return;
   const int j0 = blockIdx.y * DF_JT;
   const int nj = min(DF_JT, k - j0);
@@ -563,17 +564,20 @@ ts_dot_df_kernel(const float4 *__restrict__ V, int k, const double2 *__restrict_
   for (int j = 0; j < DF_JT; ++j) arh[j] = arl[j] = aih[j] = ail[j] = 0.f;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    float4 v[DF_JT];
+    float2 vh[DF_JT], vl[DF_JT];
 #pragma unroll
-    for (int j = 0; j < DF_JT; ++j)   // rows past the last vector reread it and add nothing
-      v[j] = __ldg(V + (long long)(j0 + (j < nj ? j : nj - 1)) * n + i);
+    for (int j = 0; j < DF_JT; ++j) {   // rows past the last vector reread it and add nothing
+      const long long o = (long long)(j0 + (j < nj ? j : nj - 1)) * n + i;
+      vh[j] = __ldg(Vh + o);
+      vl[j] = __ldg(Vl + o);
+    }
     const double2 w = __ldg(W + i);
     float wrh, wrl, wih, wil;
     split_df(w.x, wrh, wrl);
     split_df(w.y, wih, wil);
 #pragma unroll
     for (int j = 0; j < DF_JT; ++j) {
-      float vrh = v[j].x, vrl = v[j].y, vih = v[j].z, vil = v[j].w;
+      float vrh = vh[j].x, vrl = vl[j].x, vih = vh[j].y, vil = vl[j].y;
       if (j >= nj) vrh = vrl = vih = vil = 0.f;
       // conj(v) w = (vr wr + vi wi) + i (vr wi - vi wr)
       df_mac(vrh, vrl, wrh, wrl, arh[j], arl[j]);
@@ -594,39 +598,42 @@ ts_dot_df_kernel(const float4 *__restrict__ V, int k, const double2 *__restrict_
   ts_tile_reduce<DF_JT>(vals, partial);
 }
 
-// Each complex128 entry of v as (Re hi, Re lo, Im hi, Im lo) FP32: the basis
-// in the form the double-float dot reads, written once per basis vector.
+// Each complex128 entry of v as FP32 pairs in two planes: vh[i] = (Re hi,
+// Im hi), vl[i] = (Re lo, Im lo).  The basis in the form the double-float
+// dot reads (both planes) and the FP32 Gram-Schmidt correction reads (the
+// high plane: half the bytes of v), written once per basis vector.
 __global__ void __launch_bounds__(256)
-split_df_kernel(const double2 *__restrict__ v, float4 *__restrict__ vs, long long count,
-                const int *__restrict__ status) {
+split_df_kernel(const double2 *__restrict__ v, float2 *__restrict__ vh, float2 *__restrict__ vl,
+                long long count, const int *__restrict__ status) {
   if (status != nullptr && *status != 0) return;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (long long)gridDim.x * blockDim.x) {
     const double2 a = v[i];
-    float4 o;
-    split_df(a.x, o.x, o.y);
-    split_df(a.y, o.z, o.w);
-    vs[i] = o;
+    float rh, rl, ih, il;
+    split_df(a.x, rh, rl);
+    split_df(a.y, ih, il);
+    vh[i] = make_float2(rh, ih);
+    vl[i] = make_float2(rl, il);
   }
 }
 
-cudaError_t launch_split_df(const double2 *v, float4 *vs, long long count, const int *status,
-                            cudaStream_t s) {
+cudaError_t launch_split_df(const double2 *v, float2 *vh, float2 *vl, long long count,
+                            const int *status, cudaStream_t s) {
   ProfLaunch prof_(PC_TS, s);
   long long blocks = (count + 255) / 256;
   if (blocks > 4 * 1216) blocks = 4 * 1216;
   if (blocks < 1) blocks = 1;
-  split_df_kernel<<<(unsigned)blocks, 256, 0, s>>>(v, vs, count, status);
+  split_df_kernel<<<(unsigned)blocks, 256, 0, s>>>(v, vh, vl, count, status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_ts_dot_df(const float4 *V, int k, const double2 *w, long long n,
-                             double2 *partial, const int *status, cudaStream_t s) {
+cudaError_t launch_ts_dot_df(const float2 *Vh, const float2 *Vl, int k, const double2 *w,
+                             long long n, double2 *partial, const int *status, cudaStream_t s) {
   ProfLaunch prof_(PC_TS, s);
   if (k < 1 || k > 4096) return cudaErrorInvalidValue;
   dim3 grid;
   ts_dot_df_grid(n, k, &grid);
-  ts_dot_df_kernel<<<grid, TS_THREADS, 0, s>>>(V, k, w, n, partial, status);
+  ts_dot_df_kernel<<<grid, TS_THREADS, 0, s>>>(Vh, Vl, k, w, n, partial, status);
   return cudaGetLastError();
 }
 
@@ -744,10 +751,10 @@ __device__ __forceinline__ double f64_widen(float x) {
 }
 
 __global__ void __launch_bounds__(TU_THREADS)
-ts_update_correction_kernel(const double2 *__restrict__ V, int kv, const double2 *__restrict__ h,
-                            const double2 *__restrict__ hsum, int ldh,
-                            const double *__restrict__ part_w, int nbw, double2 *w, long long n,
-                            const int *__restrict__ status) {
+ts_update_correction_kernel(const double2 *__restrict__ V, const float2 *__restrict__ Vh, int kv,
+                            const double2 *__restrict__ h, const double2 *__restrict__ hsum,
+                            int ldh, const double *__restrict__ part_w, int nbw, double2 *w,
+                            long long n, const int *__restrict__ status) {
   if (status != nullptr && *status != 0) return;
   __shared__ float2 hf[TU_MAXK];
   __shared__ double2 hd[TU_MAXK];
@@ -779,8 +786,16 @@ ts_update_correction_kernel(const double2 *__restrict__ V, int kv, const double2
     if (fp32) {
       float ax = 0.f, ay = 0.f;
       for (int r = 0; r < kv; ++r) {
-        const double2 v = __ldg(V + (long long)r * n + i);
-        const float vx = f32_trunc(v.x), vy = f32_trunc(v.y);
+        float vx, vy;
+        if (Vh != nullptr) {   // the same truncation, stored: half the bytes of V
+          const float2 v = __ldg(Vh + (long long)r * n + i);
+          vx = v.x;
+          vy = v.y;
+        } else {
+          const double2 v = __ldg(V + (long long)r * n + i);
+          vx = f32_trunc(v.x);
+          vy = f32_trunc(v.y);
+        }
         const float2 c = hf[r];
         ax = fmaf(vx, c.x, fmaf(-vy, c.y, ax));
         ay = fmaf(vx, c.y, fmaf(vy, c.x, ay));
@@ -796,16 +811,16 @@ ts_update_correction_kernel(const double2 *__restrict__ V, int kv, const double2
   }
 }
 
-cudaError_t launch_ts_update_correction(const double2 *V, int kv, const double2 *h,
-                                        const double2 *hsum, int ldh, const double *part_w,
-                                        int nbw, double2 *w, long long n, const int *status,
-                                        cudaStream_t s) {
+cudaError_t launch_ts_update_correction(const double2 *V, const float2 *Vh, int kv,
+                                        const double2 *h, const double2 *hsum, int ldh,
+                                        const double *part_w, int nbw, double2 *w, long long n,
+                                        const int *status, cudaStream_t s) {
   ProfLaunch prof_(PC_TS, s);
   if (kv > TU_MAXK || kv < 1) return cudaErrorInvalidValue;
   long long blocks = (n + TU_THREADS - 1) / TU_THREADS;
   if (blocks > 1216) blocks = 1216;
-  ts_update_correction_kernel<<<(unsigned)blocks, TU_THREADS, 0, s>>>(V, kv, h, hsum, ldh, part_w,
-                                                                     nbw, w, n, status);
+  ts_update_correction_kernel<<<(unsigned)blocks, TU_THREADS, 0, s>>>(V, Vh, kv, h, hsum, ldh,
+                                                                     part_w, nbw, w, n, status);
   return cudaGetLastError();
 }
 

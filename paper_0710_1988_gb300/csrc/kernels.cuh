@@ -114,15 +114,16 @@ cudaError_t launch_ts_dot_finalize(const double2 *partial, long long n, int k, i
 // launch_ts_dot for one vector (nrhs = 1, no gamma5) in double-float
 // arithmetic (about 48 bits, on the FP32 pipe): the first pass of CGS2, whose
 // error the FP64 second pass removes.  V in the split form of
-// launch_split_df (k vectors of n float4).  Its partials (at most
-// ts_dot_partial_count(n, k, 1)) are summed by launch_ts_dot_df_finalize
+// launch_split_df (k vectors of n entries in each plane).  Its partials (at
+// most ts_dot_partial_count(n, k, 1)) are summed by launch_ts_dot_df_finalize
 // into C[j * ldc], j < k.
-cudaError_t launch_ts_dot_df(const float4 *V, int k, const double2 *w, long long n,
-                             double2 *partial, const int *status, cudaStream_t s);
-// vs[i] = (Re hi, Re lo, Im hi, Im lo) of v[i] (FP32 pairs of ~48 bits; an
-// entry outside FP32's normal range gives zeros), i < count.
-cudaError_t launch_split_df(const double2 *v, float4 *vs, long long count, const int *status,
-                            cudaStream_t s);
+cudaError_t launch_ts_dot_df(const float2 *Vh, const float2 *Vl, int k, const double2 *w,
+                             long long n, double2 *partial, const int *status, cudaStream_t s);
+// vh[i] = (Re hi, Im hi), vl[i] = (Re lo, Im lo) of v[i] (hi: the top 24
+// significant bits, lo: the next 24; an entry outside FP32's normal range
+// gives zeros), i < count.
+cudaError_t launch_split_df(const double2 *v, float2 *vh, float2 *vl, long long count,
+                            const int *status, cudaStream_t s);
 cudaError_t launch_ts_dot_df_finalize(const double2 *partial, long long n, int k, double2 *C,
                                       int ldc, const int *status, cudaStream_t s);
 // OUT[c][i] = (beta_one ? IN[c][i] : 0) + sign * sum_j V[j][i] Y[j*ldy + c],
@@ -135,10 +136,12 @@ cudaError_t launch_ts_update(const double2 *V, int kv, const double2 *Y, int ldy
 // ||h||^2 <= 1e-20 (||w0||^2 - ||hsum||^2) (part_w: Wilson-kernel partials,
 // [3 b + 2] = block b's share of ||w0||^2; hsum: column of both passes'
 // coefficients, stride ldh), else FP64 (blas.cu).
-cudaError_t launch_ts_update_correction(const double2 *V, int kv, const double2 *h,
-                                        const double2 *hsum, int ldh, const double *part_w,
-                                        int nbw, double2 *w, long long n, const int *status,
-                                        cudaStream_t s);
+// Vh: nullptr, or V's high FP32 parts in the layout of launch_split_df (read
+// instead of V on the FP32 path).
+cudaError_t launch_ts_update_correction(const double2 *V, const float2 *Vh, int kv,
+                                        const double2 *h, const double2 *hsum, int ldh,
+                                        const double *part_w, int nbw, double2 *w, long long n,
+                                        const int *status, cudaStream_t s);
 // The same product on the tensor cores (exact-split BF16 emulation to FP64
 // accuracy, tc_gemm.cu): kv <= 88, any ncol; OUT may alias IN but not V.
 // scratch: ts_update_tc_scratch_bytes(kv, ncol, n) device bytes; *err (device)

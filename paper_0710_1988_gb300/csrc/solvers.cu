@@ -244,7 +244,10 @@ int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, doubl
   size_t npart = 0;
   for (int j = 1; j <= m + 1; ++j) npart = std::max(npart, ts_dot_partial_count(n, j, 1));
   double2 *part_t = ar.take<double2>(npart);
-  float4 *Vs = ar.take<float4>((size_t)(m + 1) * n);   // the basis split for the double-float dot
+  // the basis as FP32 pairs (high and low planes) for the double-float dot
+  // and the FP32 correction
+  float2 *Vsh = ar.take<float2>((size_t)2 * (m + 1) * n);
+  float2 *Vsl = Vsh == nullptr ? nullptr : Vsh + (size_t)(m + 1) * n;
   double *part_w = ar.take<double>((size_t)nbw * 3);
   double *part_n = ar.take<double>((size_t)nbs * 2);
   double2 *H = ar.take<double2>((size_t)(m + 1) * m);
@@ -302,7 +305,7 @@ int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, doubl
   }
   WD_CK(cudaMemsetAsync(H, 0, sizeof(double2) * (m + 1) * m, s));
   RET_IF(launch_ok(launch_scale_by_inverse_entry(Va, r, c, 0, n, nullptr, s), "v1"));
-  RET_IF(launch_ok(launch_split_df(Va, Vs, n, nullptr, s), "v1 split"));
+  RET_IF(launch_ok(launch_split_df(Va, Vsh, Vsl, n, nullptr, s), "v1 split"));
 
   double2 *V = Va, *Vn = Vb;
   int j0 = 0, cycles = 0, rc = WD_NOT_CONVERGED;
@@ -320,17 +323,17 @@ int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, doubl
       // in double-float (~48 bits, FP32 pipe), the second pass's in FP64 (it
       // removes what the first left, so H = h1 + h2 is exact to FP64
       // rounding), its update in FP32 when h2 is at rounding level
-      RET_IF(launch_ok(launch_ts_dot_df(Vs, j + 1, w, n, part_t, status, s), "cgs dot1"));
+      RET_IF(launch_ok(launch_ts_dot_df(Vsh, Vsl, j + 1, w, n, part_t, status, s), "cgs dot1"));
       RET_IF(launch_ok(launch_ts_dot_df_finalize(part_t, n, j + 1, H + j, m, status, s), "cgs fin1"));
       RET_IF(launch_ok(launch_ts_update(V, j + 1, H + j, m, 1, w, w, 1, -1.0, n, status, s), "cgs upd1"));
       RET_IF(launch_ok(launch_ts_dot(V, j + 1, w, 1, 0, n, part_t, status, s), "cgs dot2"));
       RET_IF(launch_ok(launch_ts_dot_finalize(part_t, n, j + 1, 1, h2, 1, H + j, m, status, s), "cgs fin2"));
-      RET_IF(launch_ok(launch_ts_update_correction(V, j + 1, h2, H + j, m, part_w, nbw, w, n, status, s), "cgs upd2"));
+      RET_IF(launch_ok(launch_ts_update_correction(V, Vsh, j + 1, h2, H + j, m, part_w, nbw, w, n, status, s), "cgs upd2"));
       // h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}
       RET_IF(launch_ok(launch_norms(w, nullptr, part_n, n, 1, s), "norm w"));
       RET_IF(launch_ok(launch_arnoldi_normalize_finalize(part_n, nbs, part_w, nbw, H, m, j, 1e-14, status, m_eff, s), "arnoldi fin"));
       RET_IF(launch_ok(launch_scale_by_inverse_entry(V + (size_t)(j + 1) * n, w, H, (j + 1) * m + j, n, status, s), "arnoldi scale"));
-      RET_IF(launch_ok(launch_split_df(V + (size_t)(j + 1) * n, Vs + (size_t)(j + 1) * n, n, status, s), "arnoldi split"));
+      RET_IF(launch_ok(launch_split_df(V + (size_t)(j + 1) * n, Vsh + (size_t)(j + 1) * n, Vsl + (size_t)(j + 1) * n, n, status, s), "arnoldi split"));
     }
     cycles += 1;
     CycleEndArgs a;
@@ -401,7 +404,7 @@ int gmresdr_run(wd_context *h, const double2 *b, double2 *x, int m, int k, doubl
       RET_IF(launch_ok(launch_scale_by_inverse_entry(vk, vk, scal, 0, n, nullptr, s), "reorth scale"));
     }
     // the restarted basis v_1 .. v_{k+1} in split form
-    RET_IF(launch_ok(launch_split_df(V, Vs, (long long)(k + 1) * n, nullptr, s), "restart split"));
+    RET_IF(launch_ok(launch_split_df(V, Vsh, Vsl, (long long)(k + 1) * n, nullptr, s), "restart split"));
     j0 = k;
   }
   // outputs
